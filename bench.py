@@ -1,0 +1,326 @@
+"""Benchmark of the parallel multicanonical hot path on GB300.
+
+One step = the whole path on the periodic 64x64 Ising workload with p = 1024 chains:
+infinite-temperature start, 40 weight iterations of 1000 sweeps per chain (sweeps,
+histogram merge, recursion + boundary correction, thresholds), a production run of
+10^4 sweeps per chain recording (E, M), and FP64 reweighting to 512 betas in
+[0.3, 0.6].  Metric: MUCA spin-flip attempts per nanosecond.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain restatement of the method) on the
+host cores, each step a bounded sample of the same workload.  Under torchrun with
+N > 1 each rank runs an independent replica (its own seed): weak scaling, no
+collective on the data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+import workloads
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+WORKLOAD = "ising_L64_p1024"
+METRIC = "MUCA spin-flip attempts/ns on 1 GB300, plain vs batched; reweighted betas/s at 1e-6"
+L2_BYTES = 129 * 1024 * 1024
+
+REASON_BITS = {
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+    0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+    0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting",
+}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_attempts(w):
+    V = w["L"] * w["L"]
+    return w["p"] * V * (w["iterations"] * w["sweeps"] + w["production"])
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 4:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[3], 16)
+            except ValueError:
+                continue
+            for b, name in REASON_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import paper_1212_3975_gb300 as m
+    from paper_1212_3975_gb300 import build as b
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    b.build()
+    w = workloads.WORKLOADS[WORKLOAD]
+    stream = torch.cuda.Stream()
+    seed0 = w["seed"] + (rank << 20)
+    g = m.Muca(w["model"], w["L"], w["q"], w["p"], seed0, stream=stream.cuda_stream)
+    betas_h = workloads.beta_grid(w["betas"])
+    n_beta = len(betas_h)
+    betas_d = torch.tensor(betas_h, dtype=torch.float64, device="cuda")
+    out_d = torch.empty((4, n_beta), dtype=torch.float64, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    sweep_events = []
+
+    def step(seed, timed):
+        """One full pass of the hot path, inputs and outputs resident on the device."""
+        g.reset(seed)
+        for _ in range(w["iterations"]):
+            if timed:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            m.check(m.lib().muca_iterate(g.handle, w["sweeps"], None))
+            if timed:
+                e1.record(stream)
+                sweep_events.append((e0, e1))
+            m.check(m.lib().muca_update_weights(g.handle, None))
+        m.check(m.lib().muca_produce(g.handle, w["production"], None, None))
+        g.reweight(betas_d, m.MUCA_FP64, out=out_d)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(seed0 + 1000 + i, False)
+        barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        launches0 = m.kernel_launches()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        t0.record(stream)
+        for i in range(args.steps):
+            flush.zero_()                      # evict the small working set from L2
+            step(seed0 + i, True)
+        t1.record(stream)
+        barrier()
+        launches = m.kernel_launches() - launches0
+        clk = clocks.stop()
+        elapsed_ms = t0.elapsed_time(t1)
+        sweep_ms = [a.elapsed_time(z) for a, z in sweep_events]
+
+    # end to end: host buffers through the C ABI (pinned), copies inside the timing
+    E_h = torch.empty((w["production"], w["p"]), dtype=torch.int32, pin_memory=True)
+    M_h = torch.empty((w["production"], w["p"]), dtype=torch.int32, pin_memory=True)
+    H_h = torch.empty(g.n_bins, dtype=torch.int64, pin_memory=True)
+    betas_pin = torch.tensor(betas_h, dtype=torch.float64).pin_memory()
+    obs_h = torch.empty((4, n_beta), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def step_host(seed):
+        g.reset(seed)
+        for _ in range(w["iterations"]):
+            m.check(m.lib().muca_iterate(g.handle, w["sweeps"], m._ptr(H_h)))
+            m.check(m.lib().muca_update_weights(g.handle, None))
+        m.check(m.lib().muca_produce(g.handle, w["production"], m._ptr(E_h), m._ptr(M_h)))
+        m.check(m.lib().muca_reweight(g.handle, m._ptr(betas_pin), n_beta, m.MUCA_FP64,
+                                      m._ptr(obs_h[0]), m._ptr(obs_h[1]), m._ptr(obs_h[2]),
+                                      m._ptr(obs_h[3])))
+
+    with torch.cuda.stream(stream):
+        step_host(seed0 + 5000)
+        barrier()
+        h0 = time.perf_counter()
+        for i in range(e2e_steps):
+            step_host(seed0 + 6000 + i)
+        barrier()
+        e2e_s = time.perf_counter() - h0
+
+    total_ms = elapsed_ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+    attempts = workload_attempts(w)
+    value = attempts * args.steps * world / (total_ms * 1e6)
+    e2e_value = attempts * e2e_steps * world / (e2e_s * 1e9)
+
+    # roofline of the dominant kernel (sweeps of the weight iterations)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sweep_avg_ms = float(np.mean(sweep_ms))
+    att_per_launch = w["p"] * w["L"] * w["L"] * w["sweeps"]
+    inst_per_attempt = INST_PER_ATTEMPT_ISING_L64
+    achieved = inst_per_attempt * att_per_launch / (sweep_avg_ms * 1e-3) / 1e9   # Gwarp-inst/s
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 4 * sm_max * 1e6 / 1e9
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+        "frac": achieved / peak, "traffic": None,
+        "kernel": "ising_sweep_kernel (weight-iteration sweeps)",
+        "launch_ms": sweep_avg_ms,
+        "attempts_per_ns": att_per_launch / (sweep_avg_ms * 1e6),
+        "peak_note": "152 SMs x 4 schedulers x 1 warp-instruction/clock at %.0f MHz" % sm_max,
+    }
+    result = {
+        "metric": METRIC, "value": value, "unit": "attempts/ns", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "model": "ising", "L": w["L"], "p": w["p"],
+                   "iterations": w["iterations"], "sweeps": w["sweeps"],
+                   "production": w["production"], "n_beta": n_beta, "reweight": "fp64",
+                   "weights": "f64", "attempts_per_step": attempts,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas%d" % world},
+        "e2e": {"value": e2e_value, "unit": "attempts/ns",
+                "h2d_bytes_per_step": int(n_beta * 8),
+                "d2h_bytes_per_step": int(w["iterations"] * g.n_bins * 8
+                                          + 2 * w["production"] * w["p"] * 4
+                                          + 4 * n_beta * 8),
+                "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_sample(w, seconds_hint=True)
+    g.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# measured with ncu (inst_executed / attempts) on the weight-iteration sweep kernel of
+# the 64x64 Ising workload; see profiles/
+INST_PER_ATTEMPT_ISING_L64 = 50.0 / 32.0
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_sample(w, seconds_hint=False, it_sweeps=400, prod_sweeps=100):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload:
+    all p chains, one weight iteration of `it_sweeps` sweeps, the update, a production
+    run of `prod_sweeps` sweeps and the FP64 reweighting to every beta."""
+    from oracle import MucaOracle, reweight, sampler
+    betas = workloads.beta_grid(w["betas"])
+    o = MucaOracle(w["model"], w["L"], w["q"], w["p"], w["seed"])
+    t0 = time.perf_counter()
+    o.iterate(it_sweeps)
+    o.update_weights()
+    E, M = o.produce(prod_sweeps)
+    reweight.reweight_binned(w["model"], w["L"], w["q"], o.lnw,
+                             *reweight.bin_series(w["model"], w["L"], E, M), betas)
+    dt = time.perf_counter() - t0
+    att = w["p"] * w["L"] * w["L"] * (it_sweeps + prod_sweeps)
+    return {"value": att / (dt * 1e9), "unit": "attempts/ns", "cores": sampler.max_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": "%s: all %d chains, 1 iteration x %d sweeps + update + %d production "
+                      "sweeps + FP64 reweight to %d betas" % (WORKLOAD, w["p"], it_sweeps,
+                                                             prod_sweeps, len(betas))}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    w = workloads.WORKLOADS[WORKLOAD]
+    vals = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(w, it_sweeps=100, prod_sweeps=20)
+        if i >= args.warmup:
+            vals.append(s)
+    secs = sum(v["seconds"] for v in vals)
+    att = w["p"] * w["L"] * w["L"] * 120 * len(vals)
+    value = att / (secs * 1e9)
+    base = dict(vals[-1])
+    base["value"] = value
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/ns",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs * 1e3 / len(vals), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64/int", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": w["L"], "p": w["p"],
+                   "sample_per_step": base["sample"]},
+        "cpu_baseline": base,
+        "e2e": {"value": value, "unit": "attempts/ns", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * muca.h -- C ABI of the GB300 (sm_103a) parallel multicanonical library, libmuca.so.
+ *
+ * Method: Zierenberg, Marenz and Janke, "Scaling Properties of a Parallel
+ * Implementation of the Multicanonical Algorithm" (arXiv:1212.3975).  p independent
+ * Markov chains share one set of logarithmic weights ln W(E) (Sec. 2, Parallel
+ * Version); each runs single-spin-flip sweeps of the 2D Ising model (Eq. 3) or the
+ * 8-state Potts model (Eq. 4) on a periodic L x L lattice with acceptance
+ * min(1, W(E')/W(E)) (Eq. 1); their energy histograms are merged, H = sum_i H_i, and
+ * feed the recursive ln W update with boundary correction and convergence test
+ * (Secs. 2-3); a production run then records (E, M) per sweep, and Eq. 2 reweights
+ * the records to many inverse temperatures (Sec. 5 for C_V).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: MUCA_OK (0) or a negative MUCA_ERR_* code; muca_last_error()
+ *    then returns a message (thread-local, valid until the next call on the thread).
+ *  - Memory: the context owns the lattices, weights, tables, histograms and scratch
+ *    buffers on the GPU; the caller owns every pointer it passes in.  A caller buffer
+ *    may be host or device memory: device pointers (cudaMalloc, torch tensors) are
+ *    read/written asynchronously on the context's stream; host pointers are read or
+ *    written before the call returns (the call synchronises the stream).
+ *  - Streams: all work of a context runs in order on the stream given to muca_init.
+ *  - Thread safety: a context may be used by one host thread at a time.
+ *  - Energies/bins: Ising E = -sum_<ij> s_i s_j in [-2V, 2V] step 4, bin (E+2V)/4,
+ *    n_bins = V+1; Potts E = -sum_<ij> delta(s_i, s_j) in [-2V, 0], bin E+2V,
+ *    n_bins = 2V+1 (V = L*L).  Inaccessible bins (Ising E = +-(2V-4); Potts 1, 2, 3
+ *    and 5 broken bonds) keep ln W = 0 and are never entered.
+ *  - Random numbers: Philox4x32-10 with key (low 32 bits of seed, chain id) and
+ *    counter (site group, sweep, iteration, (seed >> 32) << 2 | phase); a chain's
+ *    trajectory therefore depends only on (seed, chain id, weights), never on p.
+ */
+#ifndef MUCA_H
+#define MUCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* models (Sec. 3) */
+#define MUCA_ISING 0
+#define MUCA_POTTS 1
+
+/* status codes */
+#define MUCA_OK 0
+#define MUCA_ERR_ARG (-1)     /* invalid argument or size */
+#define MUCA_ERR_CUDA (-2)    /* a CUDA call failed (message names it) */
+#define MUCA_ERR_OOM (-3)     /* device allocation failed */
+#define MUCA_ERR_TIMEOUT (-4) /* a bounded device wait gave up */
+#define MUCA_ERR_STATE (-5)   /* call not valid in the context's current state */
+#define MUCA_ERR_IO (-6)      /* checkpoint file could not be read or written */
+
+/* reweighting arithmetic for the beta x E table and its contraction */
+#define MUCA_FP64 0
+#define MUCA_FP32 1
+#define MUCA_BF16 2
+
+/* weight recursions (Sec. 2) */
+#define MUCA_RECURSION_ACCUMULATED 0 /* error-weighted, uses all past iterations */
+#define MUCA_RECURSION_SIMPLE 1      /* W^(n+1) = W^(n) / H^(n) */
+
+/* lattice staging of the sweep kernels */
+#define MUCA_STAGING_AUTO 0
+#define MUCA_STAGING_SHARED 1 /* lattices copied into shared memory for a launch */
+#define MUCA_STAGING_GLOBAL 2 /* lattices stay in global memory (L2 / HBM) */
+
+typedef struct muca_config {
+    int recursion;        /* MUCA_RECURSION_*; default accumulated */
+    int correction_width; /* bins for the boundary slope (Sec. 3); 0 -> L */
+    int chains_per_block; /* multiple of 32, <= 256; 0 -> automatic */
+    int staging;          /* MUCA_STAGING_*; 0 -> automatic */
+} muca_config;
+
+/* Convergence statistics of one merged histogram over the accessible bins (Sec. 3:
+ * full range covered and every entry within [1/2, 2] of the mean). */
+typedef struct muca_iter_stats {
+    int32_t covered;       /* every accessible bin has H > 0 */
+    int32_t flat;          /* covered and 0.5*mean <= H <= 2*mean everywhere */
+    int32_t lo, hi;        /* lowest / highest sampled accessible bin, -1 if none */
+    int64_t n_sampled;     /* accessible bins with H > 0 */
+    double min_over_mean;  /* min H / mean H */
+    double max_over_mean;  /* max H / mean H */
+    uint64_t total;        /* sum of H */
+} muca_iter_stats;
+
+typedef struct muca_ctx muca_ctx;
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *muca_last_error(void);
+
+/* Number of kernels this library has launched in the process (all contexts). */
+uint64_t muca_kernel_launches(void);
+
+/* Create p chains of the given model on an L x L periodic lattice (Sec. 3) and start
+ * them at infinite temperature: i.i.d. uniform spins, ln W = 0 (Sec. 3).
+ *  model: MUCA_ISING (q must be 2, L even, 4 <= L <= 1024) or MUCA_POTTS (q must
+ *         be 8, 3 <= L <= 255); p: 1 <= p <= 2^24 chains; seed: seed >> 32 < 2^30.
+ *  cfg:   NULL for defaults; cuda_stream: a cudaStream_t, NULL = legacy default.
+ * On success *out owns device memory until muca_destroy.
+ * Errors: MUCA_ERR_ARG, MUCA_ERR_OOM, MUCA_ERR_CUDA. */
+int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed,
+              const muca_config *cfg, void *cuda_stream);
+
+/* Release every device buffer of the context (synchronises its stream). */
+int muca_destroy(muca_ctx *ctx);
+
+/* Start the same chains again at infinite temperature with a new seed (Sec. 3):
+ * fresh i.i.d. spins, ln W = 0, recursion accumulator, histogram, production sums
+ * and all counters cleared.  No allocation; asynchronous on the context's stream.
+ * Errors: MUCA_ERR_ARG (seed >> 32 >= 2^30), MUCA_ERR_CUDA. */
+int muca_reset(muca_ctx *ctx, uint64_t seed);
+
+int muca_n_bins(const muca_ctx *ctx); /* V+1 (Ising) or 2V+1 (Potts); <0 on error */
+int muca_n_de(const muca_ctx *ctx);   /* threshold-table columns: 4 or 8 */
+int muca_num_chains(const muca_ctx *ctx);
+
+/* One weight iteration's sampling (Sec. 2, Parallel Version): every chain continues
+ * from its last state (Sec. 4) and runs n_sweeps typewriter sweeps of V updates with
+ * the current weights; after every attempt the energy bin is histogrammed.  The
+ * per-chain histograms are merged into H(E) = sum_i H_i(E) (uint64), kept in the
+ * context for muca_update_weights and copied to H_out[n_bins] when non-NULL.
+ * The iteration counter of the random streams advances by one.
+ * Errors: MUCA_ERR_ARG (n_sweeps < 1), MUCA_ERR_CUDA. */
+int muca_iterate(muca_ctx *ctx, int n_sweeps, uint64_t *H_out);
+
+/* Estimate the next weights from the last merged histogram (Secs. 2-3): the
+ * configured recursion in log form, then the boundary correction that extends
+ * ln W linearly beyond the sampled range with the slope of the innermost
+ * correction_width bins, then ln W -= max over accessible bins; the acceptance
+ * thresholds are rebuilt from the new ln W.  Convergence statistics of the histogram
+ * are written to *out when non-NULL (host pointer).
+ * Errors: MUCA_ERR_STATE (no histogram since the last update), MUCA_ERR_CUDA. */
+int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out);
+
+/* Thermalise every chain with the current weights for n_sweeps sweeps (Sec. 3:
+ * "thermalized again" before production); nothing is recorded. */
+int muca_thermalize(muca_ctx *ctx, int n_sweeps);
+
+/* Production run (Sec. 5): n_sweeps sweeps per chain at the current weights; after
+ * each sweep the chain's energy E and magnetisation M are recorded (Ising M = sum s;
+ * Potts M = q max_k N_k - V) into E_out / M_out laid out [n_sweeps][p] (int32),
+ * which may be NULL.  The records are also accumulated into per-bin exact sums
+ * (count, sum |M|, sum M^2) that muca_reweight uses.  The weights in force at the
+ * first production call after muca_init / muca_reset_samples are the ones the
+ * records are reweighted with; changing the weights in between is MUCA_ERR_STATE. */
+int muca_produce(muca_ctx *ctx, int n_sweeps, int32_t *E_out, int32_t *M_out);
+
+/* Forget the accumulated production sums. */
+int muca_reset_samples(muca_ctx *ctx);
+
+/* Time-series reweighting of all production records (Eq. 2) to n_beta inverse
+ * temperatures betas[] (host or device, FP64).  Per beta it writes
+ *   e    = <E>/V,  C = beta^2 (<E^2> - <E>^2)/V  (C_V of Sec. 5),
+ *   absm = <|M|>/Mnorm,  chi = beta V (<m^2> - <|m|>^2),  m = M/Mnorm,
+ * Mnorm = V (Ising) or (q-1) V (Potts); any output pointer may be NULL.
+ * precision selects the arithmetic of the beta x E weight table and its contraction
+ * (MUCA_FP64, MUCA_FP32, MUCA_BF16 on tensor cores); the per-beta log-sum-exp shift
+ * and the final normalisations are FP64 in every mode.
+ * Errors: MUCA_ERR_STATE (no records), MUCA_ERR_ARG. */
+int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
+                  double *e, double *C, double *absm, double *chi);
+
+/* State access (host or device buffers).
+ * lnw: [n_bins] FP64; thresholds: [n_bins][n_de] uint32, column j = ascending dE
+ * (Ising dE = -8,-4,4,8; Potts dE = -4..-1,1..4), A = 0xFFFFFFFF or u < A accepts;
+ * spins: [p][V] int8 (Ising +1/-1, Potts 0..q-1), site i = y*L + x;
+ * E, M: [p] int64 (host only); H: [n_bins] uint64 (last merged histogram);
+ * samples: n, sum|M|, sum M^2 each [n_bins] uint64. */
+int muca_get_lnw(muca_ctx *ctx, double *lnw);
+int muca_set_lnw(muca_ctx *ctx, const double *lnw); /* also rebuilds thresholds */
+int muca_get_thresholds(muca_ctx *ctx, uint32_t *thr);
+int muca_set_thresholds(muca_ctx *ctx, const uint32_t *thr); /* until next update */
+int muca_get_spins(muca_ctx *ctx, int8_t *spins);
+int muca_get_energies(muca_ctx *ctx, int64_t *E, int64_t *M);
+int muca_get_histogram(muca_ctx *ctx, uint64_t *H);
+int muca_get_samples(muca_ctx *ctx, uint64_t *n, uint64_t *sum_abs_m, uint64_t *sum_m2);
+int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
+
+/* Checkpoint / resume: the complete state (spins, E, M, Potts counts, ln W, the
+ * recursion accumulator, thresholds, counters, seed, production sums) in one file.
+ * Philox is counter-based, so a resumed run continues bit-identically. */
+int muca_save(muca_ctx *ctx, const char *path);
+int muca_load(muca_ctx **out, const char *path, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUCA_H */

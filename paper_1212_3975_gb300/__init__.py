@@ -1,0 +1,191 @@
+"""GB300 (sm_103a) parallel multicanonical (MUCA) library: Python binding.
+
+Method: Zierenberg, Marenz, Janke, arXiv:1212.3975.  The computation is in
+``libmuca.so`` (include/muca.h); this package only marshals arguments.  Buffers may be
+numpy arrays (host) or CUDA torch tensors (device; then the call is asynchronous on
+the context's stream).
+"""
+import ctypes
+
+import numpy as np
+
+from ._muca import (  # noqa: F401
+    MUCA_BF16, MUCA_FP32, MUCA_FP64, MUCA_ISING, MUCA_POTTS, MUCA_RECURSION_ACCUMULATED,
+    MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL, MUCA_STAGING_SHARED,
+    MucaConfig, MucaError, MucaIterStats, check, declared_symbols, lib)
+
+PRECISIONS = {"fp64": MUCA_FP64, "fp32": MUCA_FP32, "bf16": MUCA_BF16}
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def kernel_launches():
+    return int(lib().muca_kernel_launches())
+
+
+class Muca:
+    """One set of p chains sharing ln W(E) (a muca_ctx)."""
+
+    def __init__(self, model, L, q, p, seed, recursion=MUCA_RECURSION_ACCUMULATED,
+                 correction_width=0, chains_per_block=0, staging=MUCA_STAGING_AUTO,
+                 stream=None, _handle=None):
+        self._h = ctypes.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            cfg = MucaConfig(recursion, correction_width, chains_per_block, staging)
+            check(lib().muca_init(ctypes.byref(self._h), model, L, q, p, seed,
+                                  ctypes.byref(cfg), _ptr(stream)))
+        self.model, self.L, self.q, self.p = model, L, q, p
+        self.n_bins = lib().muca_n_bins(self._h)
+        self.n_de = lib().muca_n_de(self._h)
+        self.V = L * L
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self):
+        if self._h:
+            lib().muca_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reset(self, seed):
+        """Restart every chain at infinite temperature with a new seed (no allocation)."""
+        check(lib().muca_reset(self._h, seed))
+
+    # -- method steps ------------------------------------------------------------
+    def iterate(self, n_sweeps, H_out="host"):
+        """Sweeps of one weight iteration; returns the merged histogram (uint64)."""
+        if isinstance(H_out, str):
+            H = np.zeros(self.n_bins, dtype=np.uint64)
+            check(lib().muca_iterate(self._h, n_sweeps, _ptr(H)))
+            return H
+        check(lib().muca_iterate(self._h, n_sweeps, _ptr(H_out)))
+        return H_out
+
+    def update_weights(self):
+        st = MucaIterStats()
+        check(lib().muca_update_weights(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def thermalize(self, n_sweeps):
+        check(lib().muca_thermalize(self._h, n_sweeps))
+
+    def produce(self, n_sweeps, E_out="host", M_out="host"):
+        """Production sweeps; returns (E, M) records [n_sweeps, p] (int32)."""
+        if isinstance(E_out, str):
+            E_out = np.zeros((n_sweeps, self.p), dtype=np.int32)
+        if isinstance(M_out, str):
+            M_out = np.zeros((n_sweeps, self.p), dtype=np.int32)
+        check(lib().muca_produce(self._h, n_sweeps, _ptr(E_out), _ptr(M_out)))
+        return E_out, M_out
+
+    def reset_samples(self):
+        check(lib().muca_reset_samples(self._h))
+
+    def reweight(self, betas, precision="fp64", out=None):
+        """Eq. 2 to every beta; returns dict e, C, absm, chi (numpy FP64)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        if out is None:
+            b = np.ascontiguousarray(betas, dtype=np.float64)
+            res = {k: np.zeros(len(b)) for k in ("e", "C", "absm", "chi")}
+            check(lib().muca_reweight(self._h, _ptr(b), len(b), prec, _ptr(res["e"]),
+                                      _ptr(res["C"]), _ptr(res["absm"]), _ptr(res["chi"])))
+            return res
+        check(lib().muca_reweight(self._h, _ptr(betas), int(betas.numel()), prec,
+                                  _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(out[3])))
+        return out
+
+    # -- state -------------------------------------------------------------------
+    def get_lnw(self):
+        x = np.zeros(self.n_bins)
+        check(lib().muca_get_lnw(self._h, _ptr(x)))
+        return x
+
+    def set_lnw(self, lnw):
+        x = np.ascontiguousarray(lnw, dtype=np.float64)
+        assert x.shape == (self.n_bins,)
+        check(lib().muca_set_lnw(self._h, _ptr(x)))
+
+    def get_thresholds(self):
+        x = np.zeros((self.n_bins, self.n_de), dtype=np.uint32)
+        check(lib().muca_get_thresholds(self._h, _ptr(x)))
+        return x
+
+    def set_thresholds(self, thr):
+        x = np.ascontiguousarray(thr, dtype=np.uint32)
+        assert x.shape == (self.n_bins, self.n_de)
+        check(lib().muca_set_thresholds(self._h, _ptr(x)))
+
+    def get_spins(self):
+        x = np.zeros((self.p, self.V), dtype=np.int8)
+        check(lib().muca_get_spins(self._h, _ptr(x)))
+        return x
+
+    def get_energies(self):
+        E = np.zeros(self.p, dtype=np.int64)
+        M = np.zeros(self.p, dtype=np.int64)
+        check(lib().muca_get_energies(self._h, _ptr(E), _ptr(M)))
+        return E, M
+
+    def get_histogram(self):
+        x = np.zeros(self.n_bins, dtype=np.uint64)
+        check(lib().muca_get_histogram(self._h, _ptr(x)))
+        return x
+
+    def get_samples(self):
+        n = np.zeros(self.n_bins, dtype=np.uint64)
+        s1 = np.zeros(self.n_bins, dtype=np.uint64)
+        s2 = np.zeros(self.n_bins, dtype=np.uint64)
+        check(lib().muca_get_samples(self._h, _ptr(n), _ptr(s1), _ptr(s2)))
+        return n, s1, s2
+
+    @property
+    def iteration(self):
+        return lib().muca_get_iteration(self._h)
+
+    def save(self, path):
+        check(lib().muca_save(self._h, path.encode()))
+
+    @classmethod
+    def load(cls, path, stream=None):
+        h = ctypes.c_void_p()
+        check(lib().muca_load(ctypes.byref(h), path.encode(), _ptr(stream)))
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.n_bins = lib().muca_n_bins(h)
+        obj.n_de = lib().muca_n_de(h)
+        obj.p = lib().muca_num_chains(h)
+        obj.model = 0 if obj.n_de == 4 else 1
+        nb = obj.n_bins
+        V = nb - 1 if obj.model == 0 else (nb - 1) // 2
+        obj.V = V
+        obj.L = int(round(V ** 0.5))
+        obj.q = 2 if obj.model == 0 else 8
+        return obj

@@ -1,0 +1,606 @@
+// C ABI of libmuca: argument checks, context memory, host/device pointer handling,
+// and the order of kernel launches for each call of the parallel multicanonical
+// method (arXiv:1212.3975).  No arithmetic of the method lives here.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "muca_internal.cuh"
+
+namespace muca {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA;
+}
+
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dalloc(T **p, size_t count, const char *what)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MUCA_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    return MUCA_OK;
+}
+
+// Copy count elements from device src into a caller buffer (host or device).
+int copy_out(muca_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    if (!dst) return MUCA_OK;
+    if (is_device_ptr(dst)) {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return MUCA_OK;
+}
+
+int copy_in(muca_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    if (is_device_ptr(src)) {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return MUCA_OK;
+}
+
+void free_ctx(muca_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = {c->d_lat, c->d_E, c->d_M, c->d_cnt, c->d_lnw, c->d_P, c->d_lnw_prod, c->d_acc, c->d_thr,
+                    c->d_H, c->d_samples, c->d_stats, c->d_series, c->d_rw, c->d_wscratch,
+                    c->d_rwout};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    delete c;
+}
+
+std::vector<uint8_t> accessible_bins(int model, int L)
+{
+    const int nb = n_bins_of(model, L);
+    std::vector<uint8_t> acc(nb, 1);
+    if (model == MUCA_ISING) {
+        acc[1] = 0;
+        acc[nb - 2] = 0;
+    } else {
+        for (int k : {1, 2, 3, 5})
+            if (k < nb) acc[k] = 0;
+    }
+    return acc;
+}
+
+int check_ctx(const muca_ctx *ctx)
+{
+    if (!ctx) return fail(MUCA_ERR_ARG, "null context");
+    return MUCA_OK;
+}
+
+int alloc_buffers(muca_ctx *c)
+{
+    const size_t nb = c->n_bins;
+    int rc;
+    if ((rc = dalloc(&c->d_lat, (size_t)c->lat_words * c->p_pad, "lattice"))) return rc;
+    if ((rc = dalloc(&c->d_E, c->p_pad, "E"))) return rc;
+    if ((rc = dalloc(&c->d_M, c->p_pad, "M"))) return rc;
+    if ((rc = dalloc(&c->d_cnt, 2 * (size_t)c->p_pad, "counts"))) return rc;
+    if ((rc = dalloc(&c->d_lnw, nb, "lnW"))) return rc;
+    if ((rc = dalloc(&c->d_P, nb, "recursion accumulator"))) return rc;
+    if ((rc = dalloc(&c->d_lnw_prod, nb, "production lnW"))) return rc;
+    if ((rc = dalloc(&c->d_wscratch, nb, "update scratch"))) return rc;
+    if ((rc = dalloc(&c->d_acc, nb, "accessible bins"))) return rc;
+    if ((rc = dalloc(&c->d_thr, nb * c->n_de, "thresholds"))) return rc;
+    if ((rc = dalloc(&c->d_H, nb, "histogram"))) return rc;
+    if ((rc = dalloc(&c->d_samples, 3 * nb, "production sums"))) return rc;
+    if ((rc = dalloc(&c->d_stats, 1, "stats"))) return rc;
+    c->rw_bytes = 5 * nb * sizeof(double);
+    if ((rc = dalloc(reinterpret_cast<uint8_t **>(&c->d_rw), c->rw_bytes, "reweight scratch"))) return rc;
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_stats), sizeof(muca_iter_stats)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MUCA_ERR_OOM, "pinned allocation failed");
+    }
+    return MUCA_OK;
+}
+
+int ensure_series(muca_ctx *ctx, size_t records)
+{
+    if (ctx->series_cap >= records) return MUCA_OK;
+    if (ctx->d_series) {
+        MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->d_series);
+        ctx->d_series = nullptr;
+        ctx->series_cap = 0;
+    }
+    int rc = dalloc(&ctx->d_series, 2 * records, "production series");
+    if (rc) return rc;
+    ctx->series_cap = records;
+    return MUCA_OK;
+}
+
+}  // namespace
+}  // namespace muca
+
+using namespace muca;
+
+extern "C" {
+
+const char *muca_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t muca_kernel_launches(void) { return g_launches.load(); }
+
+int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, const muca_config *cfg,
+              void *cuda_stream)
+{
+    if (!out) return fail(MUCA_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (model == MUCA_ISING) {
+        if (q != 2) return fail(MUCA_ERR_ARG, "Ising requires q = 2");
+        if (L < 4 || L > 1024 || (L & 1)) return fail(MUCA_ERR_ARG, "Ising requires even L in [4, 1024]");
+    } else if (model == MUCA_POTTS) {
+        if (q != 8) return fail(MUCA_ERR_ARG, "Potts requires q = 8");
+        if (L < 3 || L > 255) return fail(MUCA_ERR_ARG, "Potts requires L in [3, 255]");
+    } else {
+        return fail(MUCA_ERR_ARG, "unknown model");
+    }
+    if (p < 1 || p > (1 << 24)) return fail(MUCA_ERR_ARG, "p must be in [1, 2^24]");
+    if ((seed >> 32) >= (1ull << 30)) return fail(MUCA_ERR_ARG, "seed >> 32 must be < 2^30");
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0) {
+        cudaGetLastError();
+        return fail(MUCA_ERR_CUDA, "no CUDA device available");
+    }
+    muca_config c0{MUCA_RECURSION_ACCUMULATED, 0, 0, MUCA_STAGING_AUTO};
+    if (cfg) {
+        c0 = *cfg;
+        if (c0.recursion != MUCA_RECURSION_ACCUMULATED && c0.recursion != MUCA_RECURSION_SIMPLE)
+            return fail(MUCA_ERR_ARG, "unknown recursion");
+        if (c0.correction_width < 0) return fail(MUCA_ERR_ARG, "correction_width < 0");
+        if (c0.chains_per_block < 0 || c0.chains_per_block > 256 || (c0.chains_per_block % 32))
+            return fail(MUCA_ERR_ARG, "chains_per_block must be 0 or a multiple of 32 up to 256");
+        if (c0.staging < 0 || c0.staging > 2) return fail(MUCA_ERR_ARG, "unknown staging");
+    }
+    muca_ctx *c = new muca_ctx();
+    std::memset(static_cast<void *>(c), 0, sizeof(muca_ctx));
+    c->model = model;
+    c->L = L;
+    c->q = q;
+    c->p = p;
+    c->V = L * L;
+    c->n_bins = n_bins_of(model, L);
+    c->n_de = n_de_of(model);
+    c->seed = seed;
+    c->cfg = c0;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&c->device);
+    c->row_words = model == MUCA_ISING ? (L + 31) / 32 : (L + 3) / 4;
+    c->lat_words = L * c->row_words;
+    c->p_pad = (p + 31) / 32 * 32;
+    int rc = alloc_buffers(c);
+    if (rc) {
+        free_ctx(c);
+        return rc;
+    }
+    std::vector<uint8_t> acc = accessible_bins(model, L);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->d_acc, acc.data(), acc.size(), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_lnw, 0, sizeof(double) * c->n_bins, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_P, 0, sizeof(double) * c->n_bins, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_H, 0, sizeof(uint64_t) * c->n_bins, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_samples, 0, sizeof(uint64_t) * 3 * c->n_bins, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_cnt, 0, sizeof(uint64_t) * 2 * c->p_pad, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_E, 0, sizeof(int32_t) * c->p_pad, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_M, 0, sizeof(int32_t) * c->p_pad, c->stream)) != cudaSuccess) {
+        rc = cuda_fail(e, "context initialisation");
+        free_ctx(c);
+        return rc;
+    }
+    if ((rc = launch_init_lattice(c)) || (rc = launch_thresholds(c))) {
+        free_ctx(c);
+        return rc;
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        rc = cuda_fail(e, "muca_init");
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return MUCA_OK;
+}
+
+int muca_destroy(muca_ctx *ctx)
+{
+    if (!ctx) return MUCA_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+    return MUCA_OK;
+}
+
+int muca_reset(muca_ctx *ctx, uint64_t seed)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if ((seed >> 32) >= (1ull << 30)) return fail(MUCA_ERR_ARG, "seed >> 32 must be < 2^30");
+    ctx->seed = seed;
+    MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_lnw, 0, sizeof(double) * ctx->n_bins, ctx->stream));
+    MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_P, 0, sizeof(double) * ctx->n_bins, ctx->stream));
+    MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_H, 0, sizeof(uint64_t) * ctx->n_bins, ctx->stream));
+    MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_samples, 0, sizeof(uint64_t) * 3 * ctx->n_bins, ctx->stream));
+    ctx->iteration = 0;
+    ctx->sweeps_therm = ctx->sweeps_prod = 0;
+    ctx->have_hist = 0;
+    ctx->samples_active = 0;
+    ctx->lnw_version += 1;
+    if ((rc = launch_init_lattice(ctx))) return rc;
+    return launch_thresholds(ctx);
+}
+
+int muca_n_bins(const muca_ctx *ctx) { return ctx ? ctx->n_bins : fail(MUCA_ERR_ARG, "null context"); }
+int muca_n_de(const muca_ctx *ctx) { return ctx ? ctx->n_de : fail(MUCA_ERR_ARG, "null context"); }
+int muca_num_chains(const muca_ctx *ctx) { return ctx ? ctx->p : fail(MUCA_ERR_ARG, "null context"); }
+int muca_get_iteration(const muca_ctx *ctx) { return ctx ? (int)ctx->iteration : fail(MUCA_ERR_ARG, "null context"); }
+
+int muca_iterate(muca_ctx *ctx, int n_sweeps, uint64_t *H_out)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (n_sweeps < 1) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 1");
+    MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_H, 0, sizeof(uint64_t) * ctx->n_bins, ctx->stream));
+    if ((rc = launch_sweeps(ctx, kPhaseIterate, n_sweeps, 0u, ctx->iteration, true, nullptr, nullptr, false)))
+        return rc;
+    ctx->iteration += 1;
+    ctx->have_hist = 1;
+    return copy_out(ctx, H_out, ctx->d_H, sizeof(uint64_t) * ctx->n_bins);
+}
+
+int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!ctx->have_hist) return fail(MUCA_ERR_STATE, "no histogram since the last update");
+    if ((rc = launch_update(ctx))) return rc;
+    ctx->have_hist = 0;
+    ctx->lnw_version += 1;
+    if (out) {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(muca_iter_stats), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        *out = *ctx->h_stats;
+    }
+    return MUCA_OK;
+}
+
+int muca_thermalize(muca_ctx *ctx, int n_sweeps)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (n_sweeps < 0) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 0");
+    if (n_sweeps == 0) return MUCA_OK;
+    if ((rc = launch_sweeps(ctx, kPhaseThermalize, n_sweeps, ctx->sweeps_therm, 0u, false, nullptr, nullptr, false)))
+        return rc;
+    ctx->sweeps_therm += (uint32_t)n_sweeps;
+    return MUCA_OK;
+}
+
+int muca_reset_samples(muca_ctx *ctx)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_samples, 0, sizeof(uint64_t) * 3 * ctx->n_bins, ctx->stream));
+    ctx->samples_active = 0;
+    return MUCA_OK;
+}
+
+int muca_produce(muca_ctx *ctx, int n_sweeps, int32_t *E_out, int32_t *M_out)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (n_sweeps < 1) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 1");
+    if (ctx->samples_active && ctx->samples_lnw_version != ctx->lnw_version)
+        return fail(MUCA_ERR_STATE, "weights changed since the production records started; reset samples");
+    if (!ctx->samples_active) {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(ctx->d_lnw_prod, ctx->d_lnw, sizeof(double) * ctx->n_bins,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+        ctx->samples_active = 1;
+        ctx->samples_lnw_version = ctx->lnw_version;
+    }
+    const bool dE = is_device_ptr(E_out), dM = is_device_ptr(M_out);
+    const bool host_out = (E_out && !dE) || (M_out && !dM);
+    if (!host_out) {
+        rc = launch_sweeps(ctx, kPhaseProduce, n_sweeps, ctx->sweeps_prod, 0u, false, E_out, M_out, true);
+        if (rc) return rc;
+        ctx->sweeps_prod += (uint32_t)n_sweeps;
+        return MUCA_OK;
+    }
+    // host buffers: produce in chunks through the device series buffer
+    const size_t chunk_sweeps = std::max<size_t>(1, std::min<size_t>(n_sweeps, (size_t)(64u << 20) / ctx->p));
+    if ((rc = ensure_series(ctx, chunk_sweeps * ctx->p))) return rc;
+    for (int done = 0; done < n_sweeps;) {
+        const int n = (int)std::min<size_t>(chunk_sweeps, (size_t)(n_sweeps - done));
+        int32_t *sE = ctx->d_series, *sM = ctx->d_series + ctx->series_cap;
+        rc = launch_sweeps(ctx, kPhaseProduce, n, ctx->sweeps_prod, 0u, false, sE, sM, true);
+        if (rc) return rc;
+        ctx->sweeps_prod += (uint32_t)n;
+        const size_t bytes = sizeof(int32_t) * (size_t)n * ctx->p;
+        const size_t off = (size_t)done * ctx->p;
+        if (E_out) {
+            if ((rc = copy_out(ctx, E_out + off, sE, bytes))) return rc;
+        }
+        if (M_out) {
+            if ((rc = copy_out(ctx, M_out + off, sM, bytes))) return rc;
+        }
+        done += n;
+    }
+    return MUCA_OK;
+}
+
+int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision, double *e, double *C,
+                  double *absm, double *chi)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!betas || n_beta < 1) return fail(MUCA_ERR_ARG, "need at least one beta");
+    if (precision != MUCA_FP64 && precision != MUCA_FP32 && precision != MUCA_BF16)
+        return fail(MUCA_ERR_ARG, "unknown precision");
+    if (!ctx->samples_active) return fail(MUCA_ERR_STATE, "no production records");
+    // context scratch: the four output arrays and (for host input) the betas
+    const size_t need = (size_t)5 * n_beta;
+    if (ctx->rwout_cap < need) {
+        MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (ctx->d_rwout) cudaFree(ctx->d_rwout);
+        ctx->d_rwout = nullptr;
+        ctx->rwout_cap = 0;
+        if ((rc = dalloc(&ctx->d_rwout, need, "reweight outputs"))) return rc;
+        ctx->rwout_cap = need;
+    }
+    double *d_tmp = ctx->d_rwout;
+    const double *d_betas = betas;
+    if (!is_device_ptr(betas)) {
+        MUCA_CUDA_TRY(cudaMemcpyAsync(d_tmp + 4 * (size_t)n_beta, betas, sizeof(double) * n_beta,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+        d_betas = d_tmp + 4 * (size_t)n_beta;
+    }
+    if ((rc = launch_reweight(ctx, d_betas, n_beta, precision, d_tmp))) return rc;
+    double *outs[4] = {e, C, absm, chi};
+    for (int k = 0; k < 4; ++k)
+        if ((rc = copy_out(ctx, outs[k], d_tmp + (size_t)k * n_beta, sizeof(double) * n_beta))) return rc;
+    return MUCA_OK;
+}
+
+int muca_get_lnw(muca_ctx *ctx, double *lnw)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!lnw) return fail(MUCA_ERR_ARG, "null buffer");
+    return copy_out(ctx, lnw, ctx->d_lnw, sizeof(double) * ctx->n_bins);
+}
+
+int muca_set_lnw(muca_ctx *ctx, const double *lnw)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!lnw) return fail(MUCA_ERR_ARG, "null buffer");
+    if ((rc = copy_in(ctx, ctx->d_lnw, lnw, sizeof(double) * ctx->n_bins))) return rc;
+    ctx->lnw_version += 1;
+    return launch_thresholds(ctx);
+}
+
+int muca_get_thresholds(muca_ctx *ctx, uint32_t *thr)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!thr) return fail(MUCA_ERR_ARG, "null buffer");
+    return copy_out(ctx, thr, ctx->d_thr, sizeof(uint32_t) * ctx->n_bins * ctx->n_de);
+}
+
+int muca_set_thresholds(muca_ctx *ctx, const uint32_t *thr)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!thr) return fail(MUCA_ERR_ARG, "null buffer");
+    return copy_in(ctx, ctx->d_thr, thr, sizeof(uint32_t) * ctx->n_bins * ctx->n_de);
+}
+
+int muca_get_spins(muca_ctx *ctx, int8_t *spins)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!spins) return fail(MUCA_ERR_ARG, "null buffer");
+    const size_t bytes = (size_t)ctx->V * ctx->p;
+    if (is_device_ptr(spins)) return launch_unpack_spins(ctx, spins);
+    int8_t *tmp = nullptr;
+    if ((rc = dalloc(&tmp, bytes, "spin export"))) return rc;
+    rc = launch_unpack_spins(ctx, tmp);
+    if (rc == MUCA_OK) rc = copy_out(ctx, spins, tmp, bytes);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    return rc;
+}
+
+int muca_get_energies(muca_ctx *ctx, int64_t *E, int64_t *M)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    std::vector<int32_t> e(ctx->p), m(ctx->p);
+    MUCA_CUDA_TRY(cudaMemcpyAsync(e.data(), ctx->d_E, sizeof(int32_t) * ctx->p, cudaMemcpyDeviceToHost, ctx->stream));
+    MUCA_CUDA_TRY(cudaMemcpyAsync(m.data(), ctx->d_M, sizeof(int32_t) * ctx->p, cudaMemcpyDeviceToHost, ctx->stream));
+    MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < ctx->p; ++c) {
+        if (E) E[c] = e[c];
+        if (M) M[c] = m[c];
+    }
+    return MUCA_OK;
+}
+
+int muca_get_histogram(muca_ctx *ctx, uint64_t *H)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!H) return fail(MUCA_ERR_ARG, "null buffer");
+    return copy_out(ctx, H, ctx->d_H, sizeof(uint64_t) * ctx->n_bins);
+}
+
+int muca_get_samples(muca_ctx *ctx, uint64_t *n, uint64_t *sum_abs_m, uint64_t *sum_m2)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    const size_t bytes = sizeof(uint64_t) * ctx->n_bins;
+    if ((rc = copy_out(ctx, n, ctx->d_samples, bytes))) return rc;
+    if ((rc = copy_out(ctx, sum_abs_m, ctx->d_samples + ctx->n_bins, bytes))) return rc;
+    return copy_out(ctx, sum_m2, ctx->d_samples + 2 * (size_t)ctx->n_bins, bytes);
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint: fixed header followed by the device arrays in a fixed order
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, model, L, q, p, pad0;
+    uint64_t seed;
+    muca_config cfg;
+    uint32_t iteration, sweeps_therm, sweeps_prod;
+    int32_t have_hist, samples_active, pad1;
+    uint64_t lnw_version, samples_lnw_version;
+};
+
+struct Blob {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<Blob> blobs(muca_ctx *c)
+{
+    const size_t nb = c->n_bins;
+    return {{c->d_lat, sizeof(uint32_t) * (size_t)c->lat_words * c->p_pad},
+            {c->d_E, sizeof(int32_t) * c->p_pad},
+            {c->d_M, sizeof(int32_t) * c->p_pad},
+            {c->d_cnt, sizeof(uint64_t) * 2 * c->p_pad},
+            {c->d_lnw, sizeof(double) * nb},
+            {c->d_P, sizeof(double) * nb},
+            {c->d_lnw_prod, sizeof(double) * nb},
+            {c->d_thr, sizeof(uint32_t) * nb * c->n_de},
+            {c->d_H, sizeof(uint64_t) * nb},
+            {c->d_samples, sizeof(uint64_t) * 3 * nb}};
+}
+}  // namespace
+
+int muca_save(muca_ctx *ctx, const char *path)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!path) return fail(MUCA_ERR_ARG, "null path");
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "MUCACKP1", 8);
+    h.version = 1;
+    h.model = ctx->model;
+    h.L = ctx->L;
+    h.q = ctx->q;
+    h.p = ctx->p;
+    h.seed = ctx->seed;
+    h.cfg = ctx->cfg;
+    h.iteration = ctx->iteration;
+    h.sweeps_therm = ctx->sweeps_therm;
+    h.sweeps_prod = ctx->sweeps_prod;
+    h.have_hist = ctx->have_hist;
+    h.samples_active = ctx->samples_active;
+    h.lnw_version = ctx->lnw_version;
+    h.samples_lnw_version = ctx->samples_lnw_version;
+    MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(MUCA_ERR_IO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    std::vector<uint8_t> buf;
+    for (const Blob &b : blobs(ctx)) {
+        if (!ok) break;
+        buf.resize(b.bytes);
+        if (cudaMemcpy(buf.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return cuda_fail(cudaGetLastError(), "checkpoint read-back");
+        }
+        ok = std::fwrite(buf.data(), 1, b.bytes, f) == b.bytes;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MUCA_OK : fail(MUCA_ERR_IO, std::string("write failed: ") + path);
+}
+
+int muca_load(muca_ctx **out, const char *path, void *cuda_stream)
+{
+    if (!out || !path) return fail(MUCA_ERR_ARG, "null argument");
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(MUCA_ERR_IO, std::string("cannot open ") + path);
+    CkptHeader h;
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "MUCACKP1", 8) != 0 || h.version != 1) {
+        std::fclose(f);
+        return fail(MUCA_ERR_IO, "not a checkpoint file (bad header)");
+    }
+    muca_ctx *ctx = nullptr;
+    int rc = muca_init(&ctx, h.model, h.L, h.q, h.p, h.seed, &h.cfg, cuda_stream);
+    if (rc) {
+        std::fclose(f);
+        return rc;
+    }
+    std::vector<uint8_t> buf;
+    for (const Blob &b : blobs(ctx)) {
+        buf.resize(b.bytes);
+        if (std::fread(buf.data(), 1, b.bytes, f) != b.bytes) {
+            std::fclose(f);
+            muca_destroy(ctx);
+            return fail(MUCA_ERR_IO, "checkpoint truncated");
+        }
+        if (cudaMemcpy(b.dev, buf.data(), b.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(f);
+            muca_destroy(ctx);
+            return cuda_fail(cudaGetLastError(), "checkpoint upload");
+        }
+    }
+    std::fclose(f);
+    ctx->iteration = h.iteration;
+    ctx->sweeps_therm = h.sweeps_therm;
+    ctx->sweeps_prod = h.sweeps_prod;
+    ctx->have_hist = h.have_hist;
+    ctx->samples_active = h.samples_active;
+    ctx->lnw_version = h.lnw_version;
+    ctx->samples_lnw_version = h.samples_lnw_version;
+    *out = ctx;
+    return MUCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations of libmuca (not part of the C ABI).
+//
+// Device data layout (chain-interleaved, so that the 32 chains of a warp touch 32
+// consecutive words at every step of their lockstep typewriter sweep):
+//   Ising: one bit per site, bit j of word w of row y holds site x = 32 w + j
+//          (1 = spin +1); row_words = ceil(L / 32).
+//   Potts: one byte per site, byte j of word w of row y holds site x = 4 w + j;
+//          row_words = ceil(L / 4).
+//   word k = y * row_words + w of chain c lives at lat[k * p_pad + c].
+// p_pad = p rounded up to a multiple of 32; padding chains are never touched.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/muca.h"
+
+namespace muca {
+
+constexpr uint32_t kAlways = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the 4 x 32-bit
+// S-P network, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key bumps 0x9E3779B9 /
+// 0xBB67AE85 between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * ctr.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, ctr.x);
+        const uint32_t lo1 = 0xCD9E8D57u * ctr.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, ctr.z);
+        ctr = make_uint4(hi1 ^ ctr.y ^ k0, lo1, hi0 ^ ctr.w ^ k1, lo0);
+    }
+    return ctr;
+}
+
+// counter word 3: (seed >> 32) << 2 | phase
+enum Phase : uint32_t { kPhaseInit = 0, kPhaseIterate = 1, kPhaseThermalize = 2, kPhaseProduce = 3 };
+
+__host__ __device__ inline int n_bins_of(int model, int L)
+{
+    return model == MUCA_ISING ? L * L + 1 : 2 * L * L + 1;
+}
+__host__ __device__ inline int n_de_of(int model) { return model == MUCA_ISING ? 4 : 8; }
+
+// Arguments of one sweep launch (plain values and device pointers).
+struct SweepArgs {
+    uint32_t *lat;        // [lat_words][p_pad]
+    int32_t *E;           // [p_pad] running energy
+    int32_t *M;           // [p_pad] running magnetisation (Ising) / record scratch
+    uint64_t *cnt;        // Potts packed state counts [2][p_pad]
+    const uint32_t *thr;  // [n_bins][n_de]
+    uint64_t *H;          // merged histogram [n_bins] (uint64, atomically added)
+    int32_t *E_rec;       // [n_sweeps][rec_stride] or null
+    int32_t *M_rec;
+    uint64_t *samples;    // [3][n_bins] production sums (n, sum|M|, sum M^2) or null
+    int L, q, p, p_pad, row_words, lat_words, n_bins;
+    int n_sweeps;
+    uint32_t sweep0;      // counter word 1 of the first sweep
+    uint32_t iteration;   // counter word 2
+    uint32_t ctr3;        // counter word 3 = (seed_hi << 2) | phase
+    uint32_t key0;        // low 32 bits of the seed
+    int rec_stride;       // records row stride (= p)
+};
+
+// staging flags of a sweep launch
+struct SweepPlan {
+    bool table_smem, hist_smem, lattice_smem;
+    int chains_per_block;
+    size_t smem_bytes;
+};
+
+}  // namespace muca
+
+// Host-side context (opaque to callers).
+struct muca_ctx {
+    int model, L, q, p, V, n_bins, n_de;
+    uint64_t seed;
+    muca_config cfg;
+    cudaStream_t stream;
+    int device;
+    int row_words, lat_words, p_pad;
+    // device state
+    uint32_t *d_lat;
+    int32_t *d_E, *d_M;
+    uint64_t *d_cnt;
+    double *d_lnw, *d_P, *d_lnw_prod, *d_wscratch;
+    uint8_t *d_acc;
+    uint32_t *d_thr;
+    uint64_t *d_H;
+    uint64_t *d_samples;      // [3][n_bins]
+    muca_iter_stats *d_stats;
+    muca_iter_stats *h_stats; // pinned
+    // production series scratch (used when the caller passes host or null buffers)
+    int32_t *d_series;        // [2][series_cap]
+    size_t series_cap;        // records per array
+    // reweighting scratch: per-bin table inputs, and outputs/betas of one call
+    void *d_rw;
+    size_t rw_bytes;
+    double *d_rwout;
+    size_t rwout_cap;         // doubles
+    // counters and flags
+    uint32_t iteration;
+    uint32_t sweeps_therm, sweeps_prod;
+    int have_hist;
+    int samples_active;
+    uint64_t lnw_version, samples_lnw_version;
+};
+
+namespace muca {
+
+// error plumbing (thread-local message)
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+void note_launches(uint64_t n);
+
+#define MUCA_CUDA_TRY(call)                                           \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::muca::cuda_fail(e_, #call);   \
+    } while (0)
+
+// launches (defined in the kernel translation units)
+int launch_init_lattice(muca_ctx *ctx);
+int launch_recount(muca_ctx *ctx);
+int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0,
+                  uint32_t iteration, bool hist, int32_t *E_rec, int32_t *M_rec,
+                  bool samples);
+int launch_unpack_spins(muca_ctx *ctx, int8_t *d_out);
+int launch_thresholds(muca_ctx *ctx);
+int launch_update(muca_ctx *ctx);
+int launch_stats(muca_ctx *ctx);
+int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision,
+                    double *d_out /* [4][n_beta] */);
+SweepPlan plan_sweeps(const muca_ctx *ctx);
+
+}  // namespace muca
