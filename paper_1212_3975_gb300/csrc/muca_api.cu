@@ -85,7 +85,7 @@ void free_ctx(muca_ctx *c)
     if (!c) return;
     void *ptrs[] = {c->d_lat, c->d_E, c->d_M, c->d_cnt, c->d_lnw, c->d_P, c->d_lnw_prod, c->d_acc, c->d_thr,
                     c->d_H, c->d_samples, c->d_stats, c->d_series, c->d_rw, c->d_wscratch,
-                    c->d_rwout};
+                    c->d_rwout, c->d_ktab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -126,6 +126,7 @@ int alloc_buffers(muca_ctx *c)
     if ((rc = dalloc(&c->d_wscratch, nb, "update scratch"))) return rc;
     if ((rc = dalloc(&c->d_acc, nb, "accessible bins"))) return rc;
     if ((rc = dalloc(&c->d_thr, nb * c->n_de, "thresholds"))) return rc;
+    if ((rc = dalloc(&c->d_ktab, nb * 9, "kernel thresholds"))) return rc;
     if ((rc = dalloc(&c->d_H, nb, "histogram"))) return rc;
     if ((rc = dalloc(&c->d_samples, 3 * nb, "production sums"))) return rc;
     if ((rc = dalloc(&c->d_stats, 1, "stats"))) return rc;
@@ -433,6 +434,7 @@ int muca_set_thresholds(muca_ctx *ctx, const uint32_t *thr)
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (!thr) return fail(MUCA_ERR_ARG, "null buffer");
+    ctx->ktab_dirty = 1;
     return copy_in(ctx, ctx->d_thr, thr, sizeof(uint32_t) * ctx->n_bins * ctx->n_de);
 }
 
@@ -592,6 +594,7 @@ int muca_load(muca_ctx **out, const char *path, void *cuda_stream)
         }
     }
     std::fclose(f);
+    ctx->ktab_dirty = 1;
     ctx->iteration = h.iteration;
     ctx->sweeps_therm = h.sweeps_therm;
     ctx->sweeps_prod = h.sweeps_prod;

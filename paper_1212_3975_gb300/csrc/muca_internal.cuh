@@ -58,6 +58,7 @@ struct SweepArgs {
     int32_t *M;           // [p_pad] running magnetisation (Ising) / record scratch
     uint64_t *cnt;        // Potts packed state counts [2][p_pad]
     const uint32_t *thr;  // [n_bins][n_de]
+    const uint32_t *ktab; // kernel table: Ising [n_bins][5] by unequal neighbours, Potts [n_bins][9] by dE+4
     uint64_t *H;          // merged histogram [n_bins] (uint64, atomically added)
     int32_t *E_rec;       // [n_sweeps][rec_stride] or null
     int32_t *M_rec;
@@ -95,6 +96,8 @@ struct muca_ctx {
     double *d_lnw, *d_P, *d_lnw_prod, *d_wscratch;
     uint8_t *d_acc;
     uint32_t *d_thr;
+    uint32_t *d_ktab;         // thresholds re-indexed for the sweep kernels
+    int ktab_dirty;
     uint64_t *d_H;
     uint64_t *d_samples;      // [3][n_bins]
     muca_iter_stats *d_stats;
@@ -141,5 +144,8 @@ int launch_stats(muca_ctx *ctx);
 int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision,
                     double *d_out /* [4][n_beta] */);
 SweepPlan plan_sweeps(const muca_ctx *ctx);
+int launch_ktab(muca_ctx *ctx);
+cudaError_t launch_fast_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist,
+                              bool record, cudaStream_t st);
 
 }  // namespace muca

@@ -449,8 +449,10 @@ SweepPlan plan_sweeps(const muca_ctx *ctx)
     }
     cpb = std::max(32, std::min(256, (cpb / 32) * 32));
     pl.chains_per_block = cpb;
-    const size_t table = (size_t)ctx->n_bins * ctx->n_de * 4;
-    const size_t hist = (size_t)ctx->n_bins * 4;
+    const bool fast = (ctx->L % 4) == 0;
+    const int width = fast ? (ctx->model == MUCA_ISING ? 5 : 9) : ctx->n_de;
+    const size_t table = ((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15;
+    const size_t hist = ((size_t)ctx->n_bins * 4 + 15) & ~(size_t)15;
     const size_t lat = (size_t)ctx->lat_words * 4 * cpb;
     size_t used = 0;
     pl.table_smem = table <= 96 * 1024;
@@ -468,6 +470,11 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
                   int32_t *E_rec, int32_t *M_rec, bool samples)
 {
     SweepPlan pl = plan_sweeps(ctx);
+    const bool fast = (ctx->L % 4) == 0;
+    if (fast && ctx->ktab_dirty) {
+        int rc = launch_ktab(ctx);
+        if (rc) return rc;
+    }
     if (pl.smem_bytes > (size_t)kMaxSmem)
         return fail(MUCA_ERR_ARG, "shared-memory staging does not fit: " + std::to_string(pl.smem_bytes) + " bytes");
     SweepArgs a;
@@ -476,6 +483,7 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
     a.M = ctx->d_M;
     a.cnt = ctx->d_cnt;
     a.thr = ctx->d_thr;
+    a.ktab = ctx->d_ktab;
     a.H = ctx->d_H;
     a.samples = samples ? ctx->d_samples : nullptr;
     a.L = ctx->L;
@@ -500,9 +508,10 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
         a.sweep0 = sweep0 + (uint32_t)done;
         a.E_rec = E_rec ? E_rec + (size_t)done * ctx->p : nullptr;
         a.M_rec = M_rec ? M_rec + (size_t)done * ctx->p : nullptr;
-        cudaError_t e = ctx->model == MUCA_ISING
-                            ? dispatch_mode<MUCA_ISING>(a, pl, blocks, hist, E_rec || M_rec || samples, ctx->stream)
-                            : dispatch_mode<MUCA_POTTS>(a, pl, blocks, hist, E_rec || M_rec || samples, ctx->stream);
+        const bool record = E_rec || M_rec || samples;
+        cudaError_t e = fast ? launch_fast_sweep(a, pl, ctx->model, blocks, hist, record, ctx->stream)
+                        : ctx->model == MUCA_ISING ? dispatch_mode<MUCA_ISING>(a, pl, blocks, hist, record, ctx->stream)
+                                                   : dispatch_mode<MUCA_POTTS>(a, pl, blocks, hist, record, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
         note_launches(1);
     }

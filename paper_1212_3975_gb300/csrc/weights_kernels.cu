@@ -214,6 +214,7 @@ int launch_thresholds(muca_ctx *ctx)
                                                                ctx->n_bins, ctx->n_de);
     MUCA_CUDA_TRY(cudaGetLastError());
     note_launches(1);
+    ctx->ktab_dirty = 1;
     return MUCA_OK;
 }
 

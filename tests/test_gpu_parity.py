@@ -85,7 +85,8 @@ SWEEP_CASES = [
     (ISING, 4, 5, 40, 0, 0), (ISING, 6, 37, 20, 0, 0), (ISING, 8, 8, 30, 0, 0),
     (ISING, 24, 70, 6, 64, 0), (ISING, 48, 33, 3, 32, 2), (ISING, 64, 96, 3, 0, 1),
     (ISING, 64, 40, 3, 128, 2), (ISING, 96, 9, 2, 0, 0),
-    (POTTS, 3, 7, 40, 0, 0), (POTTS, 5, 65, 20, 0, 0), (POTTS, 6, 40, 20, 64, 2),
+    (POTTS, 3, 7, 40, 0, 0), (POTTS, 4, 9, 40, 0, 0), (POTTS, 8, 33, 20, 0, 2),
+    (POTTS, 5, 65, 20, 0, 0), (POTTS, 6, 40, 20, 64, 2),
     (POTTS, 32, 40, 3, 0, 0), (POTTS, 30, 33, 3, 32, 2), (POTTS, 32, 130, 2, 128, 1)]
 
 
