@@ -14,7 +14,7 @@
 #include <stdint.h>
 #include <string>
 
-#include "../../include/muca.h"
+#include "muca.h"
 
 namespace muca {
 
@@ -40,6 +40,28 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t 
         ctr = make_uint4(hi1 ^ ctr.y ^ k0, lo1, hi0 ^ ctr.w ^ k1, lo0);
     }
     return ctr;
+}
+
+// Same generator with the per-round second key word precomputed by the caller
+// (k1r[r] = k1 + r * 0xBB67AE85); the first key word is warp-uniform (the seed).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 ctr, uint32_t k0, const uint32_t (&k1r)[10])
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t kr0 = k0 + (uint32_t)round * 0x9E3779B9u;
+        const uint32_t lo0 = 0xD2511F53u * ctr.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, ctr.x);
+        const uint32_t lo1 = 0xCD9E8D57u * ctr.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, ctr.z);
+        ctr = make_uint4(hi1 ^ ctr.y ^ kr0, lo1, hi0 ^ ctr.w ^ k1r[round], lo0);
+    }
+    return ctr;
+}
+
+__device__ __forceinline__ void philox_round_keys(uint32_t k1, uint32_t (&k1r)[10])
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) k1r[round] = k1 + (uint32_t)round * 0xBB67AE85u;
 }
 
 // counter word 3: (seed >> 32) << 2 | phase

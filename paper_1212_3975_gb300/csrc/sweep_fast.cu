@@ -22,21 +22,22 @@
 namespace muca {
 namespace {
 
+// Predicated reductions.  No "memory" clobber: the compiler may move the (unrelated)
+// table loads across them; the block's histogram is only read after __syncthreads(),
+// whose bar.sync orders all earlier shared-memory operations of the block.
 __device__ __forceinline__ void red_add_shared_if(bool p, uint32_t *addr, uint32_t v)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(addr);
     asm volatile(
         "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], %2;\n\t}" ::"r"((uint32_t)p),
-        "r"(a), "r"(v)
-        : "memory");
+        "r"(a), "r"(v));
 }
 
 __device__ __forceinline__ void red_add_global_if(bool p, uint64_t *addr, uint64_t v)
 {
     asm volatile(
         "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.global.add.u64 [%1], %2;\n\t}" ::"r"((uint32_t)p),
-        "l"(addr), "l"(v)
-        : "memory");
+        "l"(addr), "l"(v));
 }
 
 template <bool HSMEM>
@@ -93,29 +94,39 @@ __global__ void __launch_bounds__(256) ising_fast_kernel(SweepArgs a)
     uint32_t *lp = LSMEM ? s_lat + tid : a.lat + c;
     const size_t ls = LSMEM ? (size_t)cpb : (size_t)a.p_pad;
 #define LAT(k) lp[(size_t)(k) * ls]
-#define TAB(i) (TSMEM ? s_tab[(i)] : __ldg(a.ktab + (i)))
+#define TAB_BYTES(o)                                                         \
+    (TSMEM ? *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(s_tab) + (o)) \
+           : __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + (o))))
 
     if (c < a.p) {
         const int L = a.L, RW = a.row_words, V = L * L;
         const int last_bits = L - 32 * (RW - 1);
-        int bin = (a.E[c] + 2 * V) >> 2;
+        int bin = (a.E[c] + 2 * V) >> 2;  // bin after the latest attempt
+        uint32_t k1r[10];
+        philox_round_keys((uint32_t)c, k1r);
         int M = 0;
         if (RECORD) {
             int up = 0;
             for (int k = 0; k < a.lat_words; ++k) up += __popc(LAT(k));
             M = 2 * up - V;
         }
+        // Deferred form of the chain state: the table offset of an attempt is selected
+        // between two candidates computed before the previous accept is known.
+        uint32_t bin20 = 20u * (uint32_t)bin;  // 4*5*bin before the previous decision
+        uint32_t d20p = 0u;                    // its change if the previous attempt was accepted
+        bool ap = false;                       // previous attempt accepted
         int run_bin = bin;
         uint32_t run = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
             int site = 0;
+            uint4 blk = philox4x32_10_rk(make_uint4(0u, ctr1, a.iteration, a.ctr3), a.key0, k1r);
             for (int y = 0; y < L; ++y) {
                 const int kr = y * RW;
                 const int ku = (y == 0 ? L - 1 : y - 1) * RW;  // row above: updated (old for y = 0)
                 const int kd = (y == L - 1 ? 0 : y + 1) * RW;  // row below: old (new for y = L-1)
                 uint32_t R = LAT(kr), U = LAT(ku), D = LAT(kd);
-                uint32_t left = (LAT(kr + RW - 1) >> (last_bits - 1)) & 1u;  // site L-1, old
+                uint32_t lbit = (LAT(kr + RW - 1) >> (last_bits - 1)) & 1u;  // site L-1, old
                 uint32_t first_new = 0u;
                 for (int w = 0; w < RW; ++w) {
                     const bool lastw = (w == RW - 1);
@@ -126,41 +137,65 @@ __global__ void __launch_bounds__(256) ising_fast_kernel(SweepArgs a)
                         Un = LAT(ku + w + 1);
                         Dn = LAT(kd + w + 1);
                     }
-                    uint32_t ua = R ^ U, ub = R ^ D;  // unequal up / down neighbours
+                    // bit-sliced per-site sums of the neighbours that do not depend on
+                    // this row's decisions: unequal up, down and right (old) neighbours
+                    const uint32_t ua = R ^ U, ub = R ^ D;
+                    const uint32_t tr = R ^ ((R >> 1) | ((Rn & 1u) << 31));
+                    const uint32_t lo = ua ^ ub ^ tr;
+                    const uint32_t hi = (ua & ub) | (tr & (ua ^ ub));
+                    // old left neighbour differs from the site (left = site L-1 for x = 0)
+                    const uint32_t qw = R ^ ((R << 1) | lbit);
+                    uint32_t Rw = R;
                     for (int g = 0; g < nb; g += 4, site += 4) {
-                        const uint4 blk = philox4x32_10(make_uint4((uint32_t)site >> 2, ctr1, a.iteration, a.ctr3),
-                                                        a.key0, (uint32_t)c);
-                        const bool lastg = (g + 4 == nb);
+                        const uint4 nxt = philox4x32_10_rk(make_uint4(((uint32_t)site >> 2) + 1u, ctr1, a.iteration,
+                                                                   a.ctr3),
+                                                        a.key0, k1r);
+                        const bool lastg = lastw && (g + 4 == nb);
+                        const uint32_t log_ = lo >> g, hig = hi >> g, qg = qw >> g;
+                        const uint32_t uag = ua >> g, ubg = ub >> g, Rg = R >> g;
+                        const uint32_t gbit = 1u << g;
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
-                            const uint32_t s = R & 1u;
-                            uint32_t r = (R >> 1) & 1u;
-                            // right neighbour of the word's last site: next word (old), or at
-                            // the row end site 0 of this row (already updated, maybe in this group)
-                            if (k == 3) r = lastg ? (lastw ? first_new : (Rn & 1u)) : r;
-                            const uint32_t nneq = (ua & 1u) + (ub & 1u) + (s ^ r) + (s ^ left);
-                            const uint32_t A = TAB(bin * 5 + (int)nneq);
-                            const bool acc = (u < A) | (A == kAlways);
-                            const uint32_t au = acc ? 1u : 0u;
-                            R ^= au;
-                            bin += acc ? 2 - (int)nneq : 0;
-                            if (RECORD) M += acc ? 2 - 4 * (int)s : 0;
-                            left = s ^ au;
-                            if (k == 0 && w == 0 && g == 0) first_new = left;
-                            if (HIST) {
-                                const bool fl = bin != run_bin;
-                                flush_if<HSMEM>(fl, s_hist, a.H, run_bin, run);
-                                run = fl ? 1u : run + 1u;
-                                run_bin = bin;
+                            const uint32_t u = min(k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w,
+                                                   0xFFFFFFFEu);  // then u < A decides, A = 2^32-1 included
+                            uint32_t pre = ((log_ >> k) & 1u) + ((hig >> k) & 1u) * 2u;
+                            if (k == 3) {
+                                // last site of the row: its right neighbour is site 0, already updated
+                                const uint32_t pre_end =
+                                    ((uag >> 3) & 1u) + ((ubg >> 3) & 1u) + (((Rg >> 3) & 1u) ^ first_new);
+                                pre = lastg ? pre_end : pre;
                             }
-                            R = __funnelshift_r(R, R, 1);
-                            ua >>= 1;
-                            ub >>= 1;
+                            const uint32_t q = (qg >> k) & 1u;
+                            const bool rowstart = (k == 0) && (w == 0) && (g == 0);
+                            const uint32_t n0 = pre + q;                          // previous attempt rejected
+                            const uint32_t n1 = rowstart ? n0 : pre + 1u - q;     // previous attempt accepted
+                            const uint32_t b1 = bin20 + d20p;
+                            const uint32_t off = ap ? b1 + 4u * n1 : bin20 + 4u * n0;
+                            const uint32_t A = TAB_BYTES(off);
+                            const bool acc = u < A;
+                            const uint32_t nneq = ap ? n1 : n0;
+                            bin20 = ap ? b1 : bin20;
+                            d20p = 40u - 20u * nneq;
+                            bin += acc ? 2 - (int)nneq : 0;
+                            if (RECORD) M += acc ? 2 - 4 * (int)((Rg >> k) & 1u) : 0;
+                            if (k == 0 && w == 0 && g == 0) first_new = (R & 1u) ^ (acc ? 1u : 0u);
+                            Rw ^= acc ? (gbit << k) : 0u;
+                            if (HIST) {
+                                if (HSMEM) {
+                                    red_add_shared_if(true, s_hist + bin, 1u);
+                                } else {
+                                    const bool fl = bin != run_bin;
+                                    flush_if<false>(fl, s_hist, a.H, run_bin, run);
+                                    run = fl ? 1u : run + 1u;
+                                    run_bin = bin;
+                                }
+                            }
+                            ap = acc;
                         }
+                        blk = nxt;
                     }
-                    if (nb < 32) R = __funnelshift_r(R, R, 32 - nb);  // back to site order
-                    LAT(kr + w) = R;
+                    LAT(kr + w) = Rw;
+                    lbit = R >> 31;
                     R = Rn;
                     U = Un;
                     D = Dn;
@@ -178,7 +213,7 @@ __global__ void __launch_bounds__(256) ising_fast_kernel(SweepArgs a)
         if (HIST) flush_if<HSMEM>(run != 0u, s_hist, a.H, run_bin, run);
     }
 #undef LAT
-#undef TAB
+#undef TAB_BYTES
     if (LSMEM && c < a.p_pad)
         for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * cpb + tid];
     if (HIST && HSMEM) {
@@ -239,11 +274,15 @@ __global__ void __launch_bounds__(256) potts_fast_kernel(SweepArgs a)
     uint32_t *lp = LSMEM ? s_lat + tid : a.lat + c;
     const size_t ls = LSMEM ? (size_t)cpb : (size_t)a.p_pad;
 #define LAT(k) lp[(size_t)(k) * ls]
-#define TAB(i) (TSMEM ? s_tab[(i)] : __ldg(a.ktab + (i)))
+#define TAB_BYTES(o)                                                         \
+    (TSMEM ? *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(s_tab) + (o)) \
+           : __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + (o))))
 
     if (c < a.p) {
         const int L = a.L, RW = a.row_words, V = L * L;
         int bin = a.E[c] + 2 * V;
+        uint32_t k1r[10];
+        philox_round_keys((uint32_t)c, k1r);
         uint64_t cnt_lo = 0, cnt_hi = 0;
         if (RECORD) {
             uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -253,17 +292,26 @@ __global__ void __launch_bounds__(256) potts_fast_kernel(SweepArgs a)
                 cnt_hi |= (uint64_t)cnt[k + 4] << (16 * k);
             }
         }
+        // deferred chain state (see the Ising kernel): offsets in bytes of the
+        // [bin][dE+4] kernel table, 36 bytes per bin
+        uint32_t bin36 = 36u * (uint32_t)bin;
+        uint32_t d36p = 0u;
+        bool ap = false;
         int run_bin = bin;
         uint32_t run = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
             int site = 0;
+            uint4 b0 = philox4x32_10_rk(make_uint4(0u, ctr1, a.iteration, a.ctr3), a.key0, k1r);
+            uint4 b1 = philox4x32_10_rk(make_uint4(1u, ctr1, a.iteration, a.ctr3), a.key0, k1r);
             for (int y = 0; y < L; ++y) {
                 const int kr = y * RW;
                 const int ku = (y == 0 ? L - 1 : y - 1) * RW;
                 const int kd = (y == L - 1 ? 0 : y + 1) * RW;
                 uint32_t R = LAT(kr), U = LAT(ku), D = LAT(kd);
-                uint32_t left = LAT(kr + RW - 1) >> 24;  // site L-1, old
+                // candidates for the left neighbour: previous site unchanged / changed
+                uint32_t left0 = LAT(kr + RW - 1) >> 24;  // site L-1, old
+                uint32_t left1 = left0;
                 uint32_t first_new = 0u;
                 for (int w = 0; w < RW; ++w, site += 4) {
                     const bool lastw = (w == RW - 1);
@@ -273,39 +321,56 @@ __global__ void __launch_bounds__(256) potts_fast_kernel(SweepArgs a)
                         Un = LAT(ku + w + 1);
                         Dn = LAT(kd + w + 1);
                     }
-                    const uint4 b0 = philox4x32_10(make_uint4((uint32_t)site >> 1, ctr1, a.iteration, a.ctr3),
-                                                   a.key0, (uint32_t)c);
-                    const uint4 b1 = philox4x32_10(make_uint4(((uint32_t)site >> 1) + 1u, ctr1, a.iteration, a.ctr3),
-                                                   a.key0, (uint32_t)c);
+                    // random numbers of the next word, independent of the chain state
+                    const uint4 n0 = philox4x32_10_rk(make_uint4(((uint32_t)site >> 1) + 2u, ctr1, a.iteration, a.ctr3),
+                                                   a.key0, k1r);
+                    const uint4 n1 = philox4x32_10_rk(make_uint4(((uint32_t)site >> 1) + 3u, ctr1, a.iteration, a.ctr3),
+                                                   a.key0, k1r);
+                    uint32_t Rw = R;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const uint32_t u = k == 0 ? b0.x : k == 1 ? b0.z : k == 2 ? b1.x : b1.z;
+                        const uint32_t u = min(k == 0 ? b0.x : k == 1 ? b0.z : k == 2 ? b1.x : b1.z, 0xFFFFFFFEu);
                         const uint32_t pw = k == 0 ? b0.y : k == 1 ? b0.w : k == 2 ? b1.y : b1.w;
                         const uint32_t s = (R >> (8 * k)) & 0xFFu;
                         // right neighbour: next byte; after the word's last site the next word
                         // (old) or, at the row end, site 0 of this row (already updated)
                         const uint32_t r = k < 3 ? (R >> (8 * (k + 1))) & 0xFFu : (lastw ? first_new : (Rn & 0xFFu));
                         const uint32_t sn = (s + 1u + __umulhi(pw, 7u)) & 7u;
-                        // neighbours: up, down, left, right as the four bytes of one word
+                        // up, down, right neighbours as bytes 0..2; byte 3 never matches a state
                         const uint32_t ud = __byte_perm(U, D, (uint32_t)(k | ((k + 4) << 4)));
-                        const uint32_t nbw = __byte_perm(ud, left | (r << 8), 0x5410u);
-                        const int dE = zero_bytes(nbw ^ (0x01010101u * s)) - zero_bytes(nbw ^ (0x01010101u * sn));
-                        const uint32_t A = TAB(bin * 9 + dE + 4);
-                        const bool acc = (u < A) | (A == kAlways);
-                        const uint32_t mask = 0xFFu << (8 * k);
-                        R = acc ? ((R & ~mask) | (sn << (8 * k))) : R;
+                        const uint32_t nb3 = __byte_perm(ud, r | 0xFF00u, 0x5410u);
+                        const int base = zero_bytes(nb3 ^ (0x01010101u * s)) - zero_bytes(nb3 ^ (0x01010101u * sn));
+                        const int dE0 = base + (left0 == s) - (left0 == sn);
+                        const int dE1 = base + (left1 == s) - (left1 == sn);
+                        const uint32_t b1o = bin36 + d36p;
+                        const uint32_t off = ap ? b1o + 4u * (uint32_t)(dE1 + 4) : bin36 + 4u * (uint32_t)(dE0 + 4);
+                        const uint32_t A = TAB_BYTES(off);
+                        const bool acc = u < A;
+                        const int dE = ap ? dE1 : dE0;
+                        bin36 = ap ? b1o : bin36;
+                        d36p = (uint32_t)(36 * dE);
                         bin += acc ? dE : 0;
+                        const uint32_t mask = 0xFFu << (8 * k);
+                        Rw = acc ? ((Rw & ~mask) | (sn << (8 * k))) : Rw;
                         if (RECORD && acc) count_move(cnt_lo, cnt_hi, s, sn);
-                        left = acc ? sn : s;
-                        if (k == 0 && w == 0) first_new = left;
+                        if (k == 0 && w == 0) first_new = acc ? sn : s;
+                        left0 = s;
+                        left1 = sn;
                         if (HIST) {
-                            const bool fl = bin != run_bin;
-                            flush_if<HSMEM>(fl, s_hist, a.H, run_bin, run);
-                            run = fl ? 1u : run + 1u;
-                            run_bin = bin;
+                            if (HSMEM) {
+                                red_add_shared_if(true, s_hist + bin, 1u);
+                            } else {
+                                const bool fl = bin != run_bin;
+                                flush_if<false>(fl, s_hist, a.H, run_bin, run);
+                                run = fl ? 1u : run + 1u;
+                                run_bin = bin;
+                            }
                         }
+                        ap = acc;
                     }
-                    LAT(kr + w) = R;
+                    LAT(kr + w) = Rw;
+                    b0 = n0;
+                    b1 = n1;
                     R = Rn;
                     U = Un;
                     D = Dn;
@@ -329,7 +394,7 @@ __global__ void __launch_bounds__(256) potts_fast_kernel(SweepArgs a)
         if (HIST) flush_if<HSMEM>(run != 0u, s_hist, a.H, run_bin, run);
     }
 #undef LAT
-#undef TAB
+#undef TAB_BYTES
     if (LSMEM && c < a.p_pad)
         for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * cpb + tid];
     if (HIST && HSMEM) {
