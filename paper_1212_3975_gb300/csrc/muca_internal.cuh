@@ -97,6 +97,7 @@ struct SweepArgs {
 // staging flags of a sweep launch
 struct SweepPlan {
     bool table_smem, hist_smem, lattice_smem;
+    bool warp_specialized;  // decider / producer / bookkeeper warps per 32 chains
     int chains_per_block;
     size_t smem_bytes;
 };
@@ -167,6 +168,9 @@ int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precis
                     double *d_out /* [4][n_beta] */);
 SweepPlan plan_sweeps(const muca_ctx *ctx);
 int launch_ktab(muca_ctx *ctx);
+size_t ws_extra_smem();
+cudaError_t launch_ising_ws(const SweepArgs &a, const SweepPlan &pl, int blocks, bool hist, bool record,
+                            cudaStream_t st);
 cudaError_t launch_fast_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist,
                               bool record, cudaStream_t st);
 
