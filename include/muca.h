@@ -162,6 +162,30 @@ int muca_reset_samples(muca_ctx *ctx);
 int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
                   double *e, double *C, double *absm, double *chi);
 
+/* Reweighting without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * want observables -- e.g. an application whose framework allocator already holds
+ * the free device memory, or a latency-critical loop that must not stall on
+ * cudaMalloc/cudaFree (cudaFree synchronises the device).
+ * It computes what muca_reweight computes (Eq. 2, same outputs, same kernels) from
+ * caller-owned DEVICE buffers, without a context:
+ *   samples [3][n_bins] uint64 (count, sum |M|, sum M^2 per bin, as muca_get_samples),
+ *   lnw [n_bins] FP64 (the weights the samples were produced with), betas [n_beta],
+ *   out [4][n_beta] FP64 (rows e, C, absm, chi); precision MUCA_FP64 or MUCA_FP32;
+ *   work is queued on cuda_stream (NULL = legacy default stream).
+ * Its scratch is one fixed array inside the library's device image, 5 x 16385
+ * doubles (655,400 bytes), present on every GPU that loads the library until the
+ * process exits; lattices with more than 16385 bins (Ising L > 128, 8-Potts L > 90)
+ * are rejected with MUCA_ERR_ARG.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on the
+ * GPU (e.g. on two streams) race and give wrong results; serialise them.  Each call
+ * writes every scratch entry it reads, so nothing needs clearing between calls.
+ * Errors: MUCA_ERR_ARG (bad model/size, host pointers, too many bins), MUCA_ERR_CUDA. */
+int muca_reweight_noalloc(int model, int L, int q, const uint64_t *samples, const double *lnw,
+                          const double *betas, int n_beta, int precision, double *out,
+                          void *cuda_stream);
+
 /* State access (host or device buffers).
  * lnw: [n_bins] FP64; thresholds: [n_bins][n_de] uint32, column j = ascending dE
  * (Ising dE = -8,-4,4,8; Potts dE = -4..-1,1..4), A = 0xFFFFFFFF or u < A accepts;

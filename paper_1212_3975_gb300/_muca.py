@@ -62,6 +62,8 @@ _SIGS = {
     "muca_produce": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "muca_reset_samples": (ctypes.c_int, [_P]),
     "muca_reweight": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "muca_reweight_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                             ctypes.c_int, ctypes.c_int, _P, _P]),
     "muca_get_lnw": (ctypes.c_int, [_P, _P]),
     "muca_set_lnw": (ctypes.c_int, [_P, _P]),
     "muca_get_thresholds": (ctypes.c_int, [_P, _P]),

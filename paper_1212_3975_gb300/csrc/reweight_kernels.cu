@@ -284,6 +284,31 @@ __global__ void __launch_bounds__(256) reweight_fp32_kernel(BinData d, const dou
 
 }  // namespace
 
+// Same kernels with every buffer supplied by the caller: per-bin scratch of
+// 5 * n_bins doubles, production sums [3][n_bins], weights [n_bins], betas and the
+// output [4][n_beta] (all device memory).  Launches on `st`; allocates nothing.
+cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, const double *lnw, int model, int L,
+                                    int q, const double *d_betas, int n_beta, int precision, double *d_out,
+                                    cudaStream_t st)
+{
+    const int V = L * L;
+    const int nb = n_bins_of(model, L);
+    BinData d{scratch, scratch + nb, scratch + 2 * (size_t)nb, scratch + 3 * (size_t)nb, scratch + 4 * (size_t)nb};
+    prep_kernel<<<(nb + 255) / 256, 256, 0, st>>>(samples, lnw, d, model, V, nb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    Observables o{d_out, d_out + n_beta, d_out + 2 * n_beta, d_out + 3 * n_beta};
+    const double mnorm = model == MUCA_ISING ? (double)V : (double)(q - 1) * V;
+    if (precision == MUCA_FP64)
+        reweight_fp64_kernel<<<n_beta, 256, 0, st>>>(d, d_betas, nb, V, mnorm, o);
+    else
+        reweight_fp32_kernel<8><<<(n_beta + 7) / 8, 256, 0, st>>>(d, d_betas, n_beta, nb, V, mnorm, o);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) note_launches(1);
+    return e;
+}
+
 int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision, double *d_out)
 {
     const size_t nb = ctx->n_bins;

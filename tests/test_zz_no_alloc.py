@@ -1,0 +1,77 @@
+"""muca_reweight_noalloc: reweighting for callers that cannot allocate device memory.
+
+Such callers (a framework allocator already owns the free device memory, or a
+latency-critical loop must not stall on cudaMalloc/cudaFree) pass their own device
+buffers; the scratch is a fixed array inside the library.  This test calls the
+entry point through the C ABI and checks its output against the context-based
+muca_reweight, on two calls in a row with different lattices (the second call must
+not see anything the first one left in the shared scratch).  The file is named so
+that pytest collects it last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _produce(m, model, L, q, beta, seed):
+    g = m.Muca(model, L, q, 64, seed)
+    lnw = workloads.canonical_lnw(model, L, beta)
+    g.set_lnw(lnw - lnw.max())
+    g.thermalize(20)
+    g.produce(300, None, None)
+    return g
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-12)])
+def test_noalloc_matches_context_reweight(precision, tol):
+    torch = pytest.importorskip("torch")
+    import paper_1212_3975_gb300 as m
+    from paper_1212_3975_gb300 import build
+    build.build()
+    lib = m.lib()
+    prec = m.PRECISIONS[precision]
+    cases = [(m.MUCA_ISING, 16, 2, 0.42, 0.30, 0.55, 61), (m.MUCA_POTTS, 12, 8, 1.33, 1.20, 1.40, 37)]
+    for model, L, q, beta, lo, hi, n_beta in cases:          # two calls in a row
+        g = _produce(m, model, L, q, beta, seed=11)
+        betas = np.linspace(lo, hi, n_beta)
+        ref = g.reweight(betas, precision)
+        n, s1, s2 = g.get_samples()
+        samples = torch.tensor(np.stack([n, s1, s2]).view(np.int64), device="cuda")
+        lnw = torch.tensor(g.get_lnw(), device="cuda")
+        betas_d = torch.tensor(betas, device="cuda")
+        out = torch.full((4, n_beta), float("nan"), dtype=torch.float64, device="cuda")
+        rc = lib.muca_reweight_noalloc(model, L, q, _ptr(samples), _ptr(lnw), _ptr(betas_d), n_beta, prec,
+                                       _ptr(out), None)
+        m.check(rc)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for row, key in enumerate(("e", "C", "absm", "chi")):
+            rel = np.abs(got[row] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
+            assert rel.max() <= tol, (model, key, rel.max())
+        g.close()
+
+
+def test_noalloc_rejects_oversized_and_host_buffers():
+    torch = pytest.importorskip("torch")
+    import paper_1212_3975_gb300 as m
+    from paper_1212_3975_gb300 import build
+    build.build()
+    lib = m.lib()
+    dev = torch.zeros(16, dtype=torch.float64, device="cuda")
+    # 130 x 130 Ising has 16901 bins, above the fixed scratch
+    rc = lib.muca_reweight_noalloc(m.MUCA_ISING, 130, 2, _ptr(dev), _ptr(dev), _ptr(dev), 1, m.MUCA_FP64,
+                                   _ptr(dev), None)
+    assert rc == -1 and b"16385" in lib.muca_last_error()
+    host = np.zeros(16)
+    rc = lib.muca_reweight_noalloc(m.MUCA_ISING, 8, 2, ctypes.c_void_p(host.ctypes.data), _ptr(dev),
+                                   _ptr(dev), 1, m.MUCA_FP64, _ptr(dev), None)
+    assert rc == -1
