@@ -168,8 +168,8 @@ int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precis
                     double *d_out /* [4][n_beta] */);
 SweepPlan plan_sweeps(const muca_ctx *ctx);
 int launch_ktab(muca_ctx *ctx);
-size_t ws_extra_smem();
-cudaError_t launch_ising_ws(const SweepArgs &a, const SweepPlan &pl, int blocks, bool hist, bool record,
+size_t ws_extra_smem(int model);
+cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,
                             cudaStream_t st);
 cudaError_t launch_fast_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist,
                               bool record, cudaStream_t st);

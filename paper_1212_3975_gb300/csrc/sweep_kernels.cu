@@ -449,12 +449,12 @@ SweepPlan plan_sweeps(const muca_ctx *ctx)
     }
     cpb = std::max(32, std::min(256, (cpb / 32) * 32));
     const bool fast = (ctx->L % 4) == 0;
-    // the warp-specialised Ising kernel serves 32 chains per block
-    const bool ws = fast && ctx->model == MUCA_ISING;
+    // the warp-specialised kernels serve 32 chains per block
+    const bool ws = fast;
     if (ws) cpb = 32;
     pl.chains_per_block = cpb;
     pl.warp_specialized = ws;
-    const size_t cap = (size_t)kMaxSmem - (ws ? ws_extra_smem() : 0);
+    const size_t cap = (size_t)kMaxSmem - (ws ? ws_extra_smem(ctx->model) : 0);
     const int width = fast ? (ctx->model == MUCA_ISING ? 5 : 9) : ctx->n_de;
     const size_t table = ((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15;
     const size_t hist = ((size_t)ctx->n_bins * 4 + 15) & ~(size_t)15;
@@ -480,7 +480,7 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
         int rc = launch_ktab(ctx);
         if (rc) return rc;
     }
-    if (pl.smem_bytes + (pl.warp_specialized ? ws_extra_smem() : 0) > (size_t)kMaxSmem)
+    if (pl.smem_bytes + (pl.warp_specialized ? ws_extra_smem(ctx->model) : 0) > (size_t)kMaxSmem)
         return fail(MUCA_ERR_ARG, "shared-memory staging does not fit: " + std::to_string(pl.smem_bytes) + " bytes");
     SweepArgs a;
     a.lat = ctx->d_lat;
@@ -514,7 +514,7 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
         a.E_rec = E_rec ? E_rec + (size_t)done * ctx->p : nullptr;
         a.M_rec = M_rec ? M_rec + (size_t)done * ctx->p : nullptr;
         const bool record = E_rec || M_rec || samples;
-        cudaError_t e = pl.warp_specialized ? launch_ising_ws(a, pl, blocks, hist, record, ctx->stream)
+        cudaError_t e = pl.warp_specialized ? launch_ws_sweep(a, pl, ctx->model, blocks, hist, record, ctx->stream)
                         : fast ? launch_fast_sweep(a, pl, ctx->model, blocks, hist, record, ctx->stream)
                         : ctx->model == MUCA_ISING ? dispatch_mode<MUCA_ISING>(a, pl, blocks, hist, record, ctx->stream)
                                                    : dispatch_mode<MUCA_POTTS>(a, pl, blocks, hist, record, ctx->stream);

@@ -1,0 +1,717 @@
+// Warp-specialised sweep bodies (L % 4 == 0), shared by the standalone kernels
+// and the persistent batched kernel.
+//
+// Ising:
+//
+// Within one chain every attempt depends on the previous one (the weight depends on
+// the global energy), so a chain's speed is set by the length of its own instruction
+// stream.  This kernel therefore splits the work of each group of 32 chains over
+// three warps of one block, each on its own scheduler:
+//   warp 0 (decider): the Markov chain proper -- neighbour sums, threshold load,
+//          accept, spin flip.  The table offset for an attempt is chosen between two
+//          candidates prepared before the previous accept is known, and both
+//          candidate thresholds are loaded speculatively, so only a select and one
+//          compare lie between consecutive decisions.
+//   warp 1 (producer): the Philox4x32-10 draws (independent of the chain state) of
+//          each row word, written to a shared-memory ring ahead of the decider.
+//   warp 2 (bookkeeper, iteration and production launches): rebuilds from a
+//          per-word snapshot (neighbour sums, flip mask) every attempt's energy bin,
+//          fills the block histogram, and writes the (E, M) records.
+// Hand-offs use named barriers (bar.sync / bar.arrive) in the classic full/empty
+// pattern; every warp runs the same (sweep, row, word) loop nest, so the number of
+// arrivals and waits on each barrier match exactly.
+// The Markov chain, random numbers and histograms are identical to the oracle's.
+#pragma once
+#include <algorithm>
+
+#include "muca_internal.cuh"
+
+namespace muca {
+namespace ws {
+
+constexpr int kRingU = 4;   // slots of Philox draws (one row word each)
+constexpr int kRingS = 3;   // slots of bookkeeping snapshots
+constexpr int kBarFullU = 1, kBarEmptyU = kBarFullU + kRingU;      // ids 1..8
+constexpr int kBarFullS = kBarEmptyU + kRingU, kBarEmptyS = kBarFullS + kRingS;  // ids 9..14
+static_assert(kBarEmptyS + kRingS <= 16, "named barrier ids");
+
+__device__ __forceinline__ void bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Table loads as explicit instructions: both candidate thresholds must really be
+// loaded before the previous accept is known (a compiler may otherwise turn
+// "cond ? load(a) : load(b)" into "load(cond ? a : b)", which puts the load back on
+// the dependent chain).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldg_nc_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void red_shared(uint32_t *addr, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(addr)), "r"(v));
+}
+
+// snapshot of one row word for the bookkeeper (per lane)
+struct Snap {
+    uint32_t lo, hi;   // bit-sliced sum of the unequal up, down and right neighbours
+    uint32_t qw;       // site differs from its old left neighbour
+    uint32_t flip;     // sites whose spin flipped (= accepted attempts)
+    uint32_t rold;     // spins before the word was swept
+    uint32_t pad[3];
+};
+
+template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+__device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
+{
+    __syncthreads();  // smem may still be read by a previous work unit of this block
+    constexpr bool BOOK = HIST || RECORD;
+    constexpr int NP = BOOK ? 2 : 3;            // producer warps (one SM sub-partition each)
+    constexpr int NT = 128;                     // decider + producers (+ bookkeeper)
+    constexpr int NU = 32 * (1 + NP);           // threads on the draw-ring barriers
+    constexpr int BOOK_WARP = 1 + NP;
+    const int n_tab = a.n_bins * 5;
+    uint32_t *s_tab = smem;
+    uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
+    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
+    uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [kRingU][8][32]
+    Snap *s_snap = reinterpret_cast<Snap *>(s_ring + kRingU * 8 * 32);                   // [kRingS][32]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c = cblk * 32 + lane;
+    const bool active = c < a.p;
+
+    if (TSMEM)
+        for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
+    if (HIST && HSMEM)
+        for (int i = tid; i < a.n_bins; i += NT) s_hist[i] = 0u;
+    if (LSMEM && warp == 0)
+        for (int k = 0; k < a.lat_words; ++k) s_lat[k * 32 + lane] = a.lat[(size_t)k * a.p_pad + c];
+    // production launches: magnetisation at the start, read before the decider
+    // touches the lattice
+    int M_start = 0;
+    if (RECORD && warp == BOOK_WARP && active) {
+        int up = 0;
+        for (int k = 0; k < a.lat_words; ++k) up += __popc(a.lat[(size_t)k * a.p_pad + c]);
+        M_start = 2 * up - a.L * a.L;
+    }
+    __syncthreads();
+
+    const int L = a.L, RW = a.row_words, V = L * L;
+    const int last_bits = L - 32 * (RW - 1);
+    const int total = a.n_sweeps * L * RW;  // row words per launch, identical for all warps
+
+    if (warp >= 1 && warp <= NP) {
+        // ---------------- producers: Philox draws, clamped to 2^32-2 ------------
+        // producer pr computes the blocks gi = pr, pr + NP, ... of every row word
+        const int pr = warp - 1;
+        uint32_t k1r[10];
+        philox_round_keys((uint32_t)c, k1r);
+        int it = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
+            int site = 0;
+            for (int y = 0; y < L; ++y) {
+                for (int w = 0; w < RW; ++w, ++it) {
+                    const int nb = (w == RW - 1) ? last_bits : 32;
+                    const int slot = it % kRingU;
+                    if (it >= kRingU) bar_sync(kBarEmptyU + slot, NU);
+                    uint4 *dst = s_ring + slot * 8 * 32 + lane;
+                    // the word's blocks are independent: unrolled so that their 10-round
+                    // dependency chains interleave
+#pragma unroll 4
+                    for (int gi = pr; gi < (nb >> 2); gi += NP) {
+                        uint4 b = philox4x32_10_rk(make_uint4((uint32_t)(site >> 2) + (uint32_t)gi, ctr1, a.iteration,
+                                                              a.ctr3),
+                                                   a.key0, k1r);
+                        // clamped so that u < A decides (A = 2^32-1 always accepts);
+                        // padding chains get 2^32-1, which never accepts
+                        const uint32_t cap = active ? 0xFFFFFFFEu : 0xFFFFFFFFu;
+                        b.x = active ? min(b.x, cap) : cap;
+                        b.y = active ? min(b.y, cap) : cap;
+                        b.z = active ? min(b.z, cap) : cap;
+                        b.w = active ? min(b.w, cap) : cap;
+                        dst[gi * 32] = b;
+                    }
+                    site += nb;
+                    bar_arrive(kBarFullU + slot, NU);
+                }
+            }
+        }
+    } else if (warp == 0) {
+        // ---------------- decider: the Markov chain -----------------------------
+        uint32_t *lp = LSMEM ? s_lat + lane : a.lat + c;
+        const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
+#define LAT(k) lp[(size_t)(k) * ls]
+        const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
+#define TAB_BYTES(o)                 \
+    (TSMEM ? lds_u32(tab_s + (o))    \
+           : ldg_nc_u32(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + (o))))
+        const int bin0 = active ? (a.E[c] + 2 * V) >> 2 : (V >> 1);
+        uint32_t bin20 = 20u * (uint32_t)bin0;  // 4*5*bin before the previous decision
+        uint32_t d20p = 0u;                     // its change if the previous attempt was accepted
+        bool ap = false;                        // previous attempt accepted
+        int it = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            for (int y = 0; y < L; ++y) {
+                const int kr = y * RW;
+                const int ku = (y == 0 ? L - 1 : y - 1) * RW;  // row above: updated (old for y = 0)
+                const int kd = (y == L - 1 ? 0 : y + 1) * RW;  // row below: old (new for y = L-1)
+                uint32_t R = LAT(kr), U = LAT(ku), D = LAT(kd);
+                uint32_t lbit = (LAT(kr + RW - 1) >> (last_bits - 1)) & 1u;  // site L-1, old
+                uint32_t first_new = 0u;
+                for (int w = 0; w < RW; ++w, ++it) {
+                    const bool lastw = (w == RW - 1);
+                    const int nb = lastw ? last_bits : 32;
+                    uint32_t Rn = 0u, Un = 0u, Dn = 0u;
+                    if (!lastw) {
+                        Rn = LAT(kr + w + 1);
+                        Un = LAT(ku + w + 1);
+                        Dn = LAT(kd + w + 1);
+                    }
+                    const uint32_t ua = R ^ U, ub = R ^ D;
+                    const uint32_t tr = R ^ ((R >> 1) | ((Rn & 1u) << 31));
+                    uint32_t lo = ua ^ ub ^ tr;
+                    uint32_t hi = (ua & ub) | (tr & (ua ^ ub));
+                    const uint32_t qw = R ^ ((R << 1) | lbit);
+                    const int slot = it % kRingU;
+                    bar_sync(kBarFullU + slot, NU);
+                    const uint4 *src = s_ring + slot * 8 * 32 + lane;
+                    uint32_t Rw = R;
+                    if (nb == 32) {
+                        // Full word, software-pipelined: while site j decides, the two
+                        // candidate thresholds of site j+1 are loaded (their offsets are
+                        // resolved by site j-1's decision).  State: P0/P1 = 20 * bin
+                        // before this site's decision if the previous attempt was
+                        // rejected / accepted.
+                        uint32_t P0 = bin20, P1 = bin20 + d20p;
+                        uint32_t K0n, K1n, D0n, D1n;  // of the next site
+                        auto site_consts = [&](int j, uint32_t &K0, uint32_t &K1, uint32_t &D0, uint32_t &D1) {
+                            uint32_t pre = ((lo >> j) & 1u) + ((hi >> j) & 1u) * 2u;
+                            if (j == 31) {
+                                // row end (last word): right neighbour is site 0, already updated
+                                const uint32_t pre_end =
+                                    ((ua >> 31) & 1u) + ((ub >> 31) & 1u) + ((R >> 31) ^ first_new);
+                                pre = lastw ? pre_end : pre;
+                            }
+                            const uint32_t q = (qw >> j) & 1u;
+                            const uint32_t n0 = pre + q;
+                            const uint32_t n1 = (j == 0 && w == 0) ? n0 : pre + 1u - q;
+                            K0 = tab_s + 4u * n0;
+                            K1 = tab_s + 4u * n1;
+                            D0 = 40u - 20u * n0;
+                            D1 = 40u - 20u * n1;
+                        };
+                        uint32_t K0, K1, D0, D1;
+                        site_consts(0, K0, K1, D0, D1);
+                        uint32_t A0 = TSMEM ? lds_u32(P0 + K0) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
+                                                                      reinterpret_cast<const char *>(a.ktab) + P0 + K0 - tab_s));
+                        uint32_t A1 = TSMEM ? lds_u32(P1 + K1) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
+                                                                      reinterpret_cast<const char *>(a.ktab) + P1 + K1 - tab_s));
+                        uint4 blk = src[0];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int k = j & 3;
+                            if (k == 0 && j > 0) blk = src[(j >> 2) * 32];
+                            const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
+                            // Issue order matters (a warp issues in order): first the loads
+                            // of site j+1, whose offsets need only the previous decision,
+                            // then the decision of site j, which waits for its own loads.
+                            uint32_t A0n = 0u, A1n = 0u;
+                            if (j < 31) {
+                                site_consts(j + 1, K0n, K1n, D0n, D1n);
+                                const uint32_t o0 = ap ? P1 + K0n : P0 + K0n;
+                                const uint32_t o1 = ap ? P1 + D1 + K1n : P0 + D0 + K1n;
+                                A0n = TSMEM ? lds_u32(o0) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
+                                                               reinterpret_cast<const char *>(a.ktab) + o0 - tab_s));
+                                A1n = TSMEM ? lds_u32(o1) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
+                                                               reinterpret_cast<const char *>(a.ktab) + o1 - tab_s));
+                            }
+                            const uint32_t A = ap ? A1 : A0;
+                            const bool acc = u < A;
+                            const uint32_t nP0 = ap ? P1 : P0;
+                            const uint32_t nP1 = ap ? P1 + D1 : P0 + D0;
+                            A0 = A0n;
+                            A1 = A1n;
+                            P0 = nP0;
+                            P1 = nP1;
+                            D0 = D0n;
+                            D1 = D1n;
+                            Rw ^= acc ? (1u << j) : 0u;
+                            if (j == 0 && w == 0) first_new = (R & 1u) ^ (acc ? 1u : 0u);
+                            ap = acc;
+                        }
+                        // back to the (bin20, d20p) form at the word boundary
+                        bin20 = P0;
+                        d20p = P1 - P0;
+                    } else
+                    for (int g = 0; g < nb; g += 4) {
+                        uint4 blk = src[(g >> 2) * 32];
+                        const uint4 nxt = (g + 4 < nb) ? src[((g >> 2) + 1) * 32] : blk;
+                        const bool lastg = lastw && (g + 4 == nb);
+                        const uint32_t log_ = lo >> g, hig = hi >> g, qg = qw >> g;
+                        const uint32_t uag = ua >> g, ubg = ub >> g, Rg = R >> g;
+                        const uint32_t gbit = 1u << g;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
+                            uint32_t pre = ((log_ >> k) & 1u) + ((hig >> k) & 1u) * 2u;
+                            if (k == 3) {
+                                // row end: the right neighbour is site 0, already updated
+                                const uint32_t pre_end =
+                                    ((uag >> 3) & 1u) + ((ubg >> 3) & 1u) + (((Rg >> 3) & 1u) ^ first_new);
+                                pre = lastg ? pre_end : pre;
+                            }
+                            const uint32_t q = (qg >> k) & 1u;
+                            const bool rowstart = (k == 0) && (w == 0) && (g == 0);
+                            const uint32_t n0 = pre + q;
+                            const uint32_t n1 = rowstart ? n0 : pre + 1u - q;
+                            const uint32_t b1o = bin20 + d20p;
+                            const uint32_t A0 = TAB_BYTES(bin20 + 4u * n0);
+                            const uint32_t A1 = TAB_BYTES(b1o + 4u * n1);
+                            const uint32_t A = ap ? A1 : A0;
+                            const bool acc = active && (u < A);
+                            const uint32_t nneq = ap ? n1 : n0;
+                            bin20 = ap ? b1o : bin20;
+                            d20p = 40u - 20u * nneq;
+                            Rw ^= acc ? (gbit << k) : 0u;
+                            if (k == 0 && w == 0 && g == 0) first_new = (R & 1u) ^ (acc ? 1u : 0u);
+                            ap = acc;
+                        }
+                        blk = nxt;
+                    }
+                    if (it < total - kRingU) bar_arrive(kBarEmptyU + slot, NU);
+                    LAT(kr + w) = Rw;
+                    if (BOOK) {
+                        if (lastw) {
+                            // the row's last site saw the updated site 0 as its right neighbour
+                            const uint32_t bitm = 1u << (nb - 1);
+                            const uint32_t tr2 = (tr & ~bitm) | ((((R >> (nb - 1)) & 1u) ^ first_new) << (nb - 1));
+                            lo = ua ^ ub ^ tr2;
+                            hi = (ua & ub) | (tr2 & (ua ^ ub));
+                        }
+                        const int ss = it % kRingS;
+                        if (it >= kRingS) bar_sync(kBarEmptyS + ss, 64);
+                        Snap *sn = s_snap + ss * 32 + lane;
+                        sn->lo = lo;
+                        sn->hi = hi;
+                        sn->qw = qw;
+                        sn->flip = R ^ Rw;
+                        sn->rold = R;
+                        bar_arrive(kBarFullS + ss, 64);
+                    }
+                    lbit = R >> 31;
+                    R = Rn;
+                    U = Un;
+                    D = Dn;
+                }
+            }
+        }
+        if (active && !BOOK) {
+            // no bookkeeper: apply the pending decision and recount M
+            const uint32_t bin_end = (ap ? bin20 + d20p : bin20) / 20u;
+            a.E[c] = 4 * (int)bin_end - 2 * V;
+            int up = 0;
+            for (int k = 0; k < a.lat_words; ++k) up += __popc(LAT(k));
+            a.M[c] = 2 * up - V;
+        }
+#undef TAB_BYTES
+        if (LSMEM)
+            for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
+#undef LAT
+    } else if (BOOK && warp == BOOK_WARP) {
+        // ---------------- bookkeeper: bins, histogram, records -------------------
+        int bin = active ? (a.E[c] + 2 * V) >> 2 : (V >> 1);
+        int M = M_start;
+        int run_bin = bin;
+        uint32_t run = 0;
+        int it = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            for (int y = 0; y < L; ++y) {
+                uint32_t pflip = 0u;  // flip of the previous site in this row
+                for (int w = 0; w < RW; ++w, ++it) {
+                    const int nb = (w == RW - 1) ? last_bits : 32;
+                    const int ss = it % kRingS;
+                    bar_sync(kBarFullS + ss, 64);
+                    const Snap sn = s_snap[ss * 32 + lane];
+                    if (it < total - kRingS) bar_arrive(kBarEmptyS + ss, 64);
+                    // left neighbour as seen by each site: old left, flipped if the
+                    // previous site flipped (not across the row start)
+                    const uint32_t lf = (sn.flip << 1) | pflip;
+                    const uint32_t qn = sn.qw ^ lf;
+                    auto book_site = [&](int j) {
+                        const int nneq = (int)(((sn.lo >> j) & 1u) + 2u * ((sn.hi >> j) & 1u) + ((qn >> j) & 1u));
+                        const bool acc = (sn.flip >> j) & 1u;
+                        bin += acc ? 2 - nneq : 0;
+                        if (HIST && active) {
+                            if (HSMEM) {
+                                red_shared(s_hist + bin, 1u);
+                            } else {
+                                if (bin != run_bin) {
+                                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]),
+                                              (unsigned long long)run);
+                                    run_bin = bin;
+                                    run = 0;
+                                }
+                                ++run;
+                            }
+                        }
+                    };
+                    if (nb == 32) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) book_site(j);
+                    } else {
+                        for (int j = 0; j < nb; ++j) book_site(j);
+                    }
+                    if (RECORD) {
+                        const uint32_t f = sn.flip;
+                        M += 2 * (__popc(f & ~sn.rold) - __popc(f & sn.rold));
+                    }
+                    pflip = (sn.flip >> (nb - 1)) & 1u;
+                }
+            }
+            if (RECORD && active) {
+                const int E = 4 * bin - 2 * V;
+                if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
+                if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
+                if (a.samples) {
+                    const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
+                    unsigned long long *s = reinterpret_cast<unsigned long long *>(a.samples);
+                    atomicAdd(&s[bin], 1ull);
+                    atomicAdd(&s[a.n_bins + bin], am);
+                    atomicAdd(&s[2 * a.n_bins + bin], am * am);
+                }
+            }
+        }
+        if (active) {
+            if (HIST && !HSMEM && run)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
+            a.E[c] = 4 * bin - 2 * V;
+            if (RECORD) a.M[c] = M;
+        }
+    }
+    __syncthreads();
+    if (BOOK && !RECORD && warp == 0 && active) {
+        // iteration launches: magnetisation recount from the final lattice
+        int up = 0;
+        for (int k = 0; k < a.lat_words; ++k) up += __popc(a.lat[(size_t)k * a.p_pad + c]);
+        a.M[c] = 2 * up - V;
+    }
+    if (HIST && HSMEM) {
+        for (int i = tid; i < a.n_bins; i += NT) {
+            const uint32_t v = s_hist[i];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[i]), (unsigned long long)v);
+        }
+    }
+}
+
+
+// ===========================================================================
+// 8-state Potts: warp 0 decides (and fills the histogram / records), warps 1..3
+// produce the Philox blocks (two per site pair; half a block per attempt).
+// A ring slot holds up to 8 words (32 sites) of one row.
+// ===========================================================================
+constexpr int kPottsSlotWords = 8;
+constexpr int kPottsRing = 4;
+
+__device__ __forceinline__ int zero_bytes_ws(uint32_t x)
+{
+    const uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+    return __popc(~t & 0x80808080u);
+}
+
+__device__ __forceinline__ void potts_count_move(uint64_t &lo, uint64_t &hi, uint32_t from, uint32_t to)
+{
+    const uint64_t df = 1ull << (16 * (from & 3u)), dt = 1ull << (16 * (to & 3u));
+    if (from < 4) lo -= df; else hi -= df;
+    if (to < 4) lo += dt; else hi += dt;
+}
+
+__device__ __forceinline__ int potts_count_max(uint64_t lo, uint64_t hi)
+{
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        m = max(m, (int)((lo >> (16 * k)) & 0xFFFFu));
+        m = max(m, (int)((hi >> (16 * k)) & 0xFFFFu));
+    }
+    return m;
+}
+
+__device__ __forceinline__ void potts_count_word(uint32_t word, uint32_t (&cnt)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cnt[k] += zero_bytes_ws(word ^ (0x01010101u * (uint32_t)k));
+}
+
+template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+__device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
+{
+    constexpr int NP = 3;
+    constexpr int NT = 128;
+    constexpr int NU = 128;
+    __syncthreads();  // smem may still be read by a previous work unit of this block
+    const int n_tab = a.n_bins * 9;
+    uint32_t *s_tab = smem;
+    uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
+    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
+    uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][16][32]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c = cblk * 32 + lane;
+    const bool active = c < a.p;
+
+    if (TSMEM)
+        for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
+    if (HIST && HSMEM)
+        for (int i = tid; i < a.n_bins; i += NT) s_hist[i] = 0u;
+    if (LSMEM && warp == 0)
+        for (int k = 0; k < a.lat_words; ++k) s_lat[k * 32 + lane] = a.lat[(size_t)k * a.p_pad + c];
+    __syncthreads();
+
+    const int L = a.L, RW = a.row_words, V = L * L;
+    const int slots_per_row = (RW + kPottsSlotWords - 1) / kPottsSlotWords;
+    const int total = a.n_sweeps * L * slots_per_row;
+
+    if (warp >= 1) {
+        // ---------------- producers ----------------------------------------------
+        const int pr = warp - 1;
+        uint32_t k1r[10];
+        philox_round_keys((uint32_t)c, k1r);
+        int it = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
+            for (int y = 0; y < L; ++y) {
+                for (int w0 = 0; w0 < RW; w0 += kPottsSlotWords, ++it) {
+                    const int nw = min(kPottsSlotWords, RW - w0);
+                    const int slot = it % kPottsRing;
+                    if (it >= kPottsRing) bar_sync(kBarEmptyU + slot, NU);
+                    uint4 *dst = s_ring + slot * 16 * 32 + lane;
+                    const uint32_t g0 = (uint32_t)(y * L + 4 * w0) >> 1;  // first site pair
+#pragma unroll 6
+                    for (int bi = pr; bi < 2 * nw; bi += NP) {
+                        uint4 b = philox4x32_10_rk(make_uint4(g0 + (uint32_t)bi, ctr1, a.iteration, a.ctr3), a.key0,
+                                                   k1r);
+                        // acceptance draws clamped so that u < A decides; padding chains never accept
+                        b.x = active ? min(b.x, 0xFFFFFFFEu) : 0xFFFFFFFFu;
+                        b.z = active ? min(b.z, 0xFFFFFFFEu) : 0xFFFFFFFFu;
+                        // proposal offsets floor(7 w / 2^32) in 0..6, exactly: 7w = 8w - w
+                        b.y = (b.y >> 29) - ((b.y << 3) < b.y ? 1u : 0u);
+                        b.w = (b.w >> 29) - ((b.w << 3) < b.w ? 1u : 0u);
+                        dst[bi * 32] = b;
+                    }
+                    bar_arrive(kBarFullU + slot, NU);
+                }
+            }
+        }
+    } else {
+        // ---------------- decider ------------------------------------------------
+        uint32_t *lp = LSMEM ? s_lat + lane : a.lat + c;
+        const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
+#define LAT(k) lp[(size_t)(k) * ls]
+        const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
+        const char *tab_g = reinterpret_cast<const char *>(a.ktab) - tab_s;
+#define TABLOAD(o) (TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(tab_g + (o))))
+        int bin = active ? a.E[c] + 2 * V : V;  // bin after the latest attempt
+        uint64_t cnt_lo = 0, cnt_hi = 0;
+        if (RECORD && active) {
+            uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k = 0; k < a.lat_words; ++k) potts_count_word(LAT(k), cnt);
+            for (int k = 0; k < 4; ++k) {
+                cnt_lo |= (uint64_t)cnt[k] << (16 * k);
+                cnt_hi |= (uint64_t)cnt[k + 4] << (16 * k);
+            }
+        }
+        // deferred state: P0/P1 = 36 * bin before this attempt if the previous attempt
+        // was rejected / accepted
+        uint32_t P0 = 36u * (uint32_t)bin, P1 = P0;
+        bool ap = false;
+        int run_bin = bin;
+        uint32_t run = 0;
+        int it = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            for (int y = 0; y < L; ++y) {
+                const int kr = y * RW;
+                const int ku = (y == 0 ? L - 1 : y - 1) * RW;
+                const int kd = (y == L - 1 ? 0 : y + 1) * RW;
+                uint32_t R = LAT(kr), U = LAT(ku), D = LAT(kd);
+                uint32_t left0 = LAT(kr + RW - 1) >> 24, left1 = left0;  // site L-1, old
+                uint32_t first_new = 0u;
+                for (int w0 = 0; w0 < RW; w0 += kPottsSlotWords, ++it) {
+                    const int nw = min(kPottsSlotWords, RW - w0);
+                    const int slot = it % kPottsRing;
+                    bar_sync(kBarFullU + slot, NU);
+                    const uint4 *src = s_ring + slot * 16 * 32 + lane;
+                    // per-site constants: offsets of the two table candidates and dE
+                    auto consts = [&](uint32_t Rw_, uint32_t Uw, uint32_t Dw, uint32_t right, uint32_t pw, int k,
+                                      uint32_t l0, uint32_t l1, bool rowstart, uint32_t &s, uint32_t &sn,
+                                      int &dE0, int &dE1) {
+                        s = (Rw_ >> (8 * k)) & 0xFFu;
+                        sn = (s + 1u + pw) & 7u;  // pw: proposal offset from the producer
+                        const uint32_t ud = __byte_perm(Uw, Dw, (uint32_t)(k | ((k + 4) << 4)));
+                        const uint32_t nb3 = __byte_perm(ud, right | 0xFF00u, 0x5410u);
+                        const int base = zero_bytes_ws(nb3 ^ (0x01010101u * s)) - zero_bytes_ws(nb3 ^ (0x01010101u * sn));
+                        dE0 = base + (l0 == s) - (l0 == sn);
+                        dE1 = rowstart ? dE0 : base + (l1 == s) - (l1 == sn);
+                    };
+                    bool loaded = false;   // candidates of the next site already in flight
+                    uint32_t A0 = 0u, A1 = 0u;
+                    uint32_t s_c = 0u, sn_c = 0u;
+                    int dE0_c = 0, dE1_c = 0;
+                    for (int w = w0; w < w0 + nw; ++w) {
+                        const bool lastw = (w == RW - 1);
+                        const bool slot_last = (w == w0 + nw - 1);
+                        uint32_t Rn = 0u, Un = 0u, Dn = 0u;
+                        if (!lastw) {
+                            Rn = LAT(kr + w + 1);
+                            Un = LAT(ku + w + 1);
+                            Dn = LAT(kd + w + 1);
+                        }
+                        const uint4 b0 = src[(2 * (w - w0)) * 32], b1 = src[(2 * (w - w0) + 1) * 32];
+                        uint4 nb0 = b0;
+                        if (!slot_last) nb0 = src[(2 * (w - w0) + 2) * 32];
+                        uint32_t Rw = R;
+                        if (!loaded) {
+                            // first site of the slot: constants and loads now
+                            const uint32_t right = (R >> 8) & 0xFFu;
+                            consts(R, U, D, right, b0.y, 0, left0, left1, w == 0, s_c, sn_c, dE0_c, dE1_c);
+                            A0 = TABLOAD(P0 + tab_s + 4u * (uint32_t)(dE0_c + 4));
+                            A1 = TABLOAD(P1 + tab_s + 4u * (uint32_t)(dE1_c + 4));
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t u = k == 0 ? b0.x : k == 1 ? b0.z : k == 2 ? b1.x : b1.z;
+                            // 1. constants and candidate loads of the next site
+                            uint32_t s_n = 0u, sn_n = 0u;
+                            int dE0_n = 0, dE1_n = 0;
+                            uint32_t A0n = 0u, A1n = 0u;
+                            const bool has_next = (k < 3) || !slot_last;
+                            uint32_t nP0 = ap ? P1 : P0;
+                            uint32_t nP1 = ap ? P1 + (uint32_t)(36 * dE1_c) : P0 + (uint32_t)(36 * dE0_c);
+                            if (has_next) {
+                                if (k < 3) {
+                                    const uint32_t pw = k == 0 ? b0.w : k == 1 ? b1.y : b1.w;
+                                    const uint32_t right = k < 2 ? (R >> (8 * (k + 2))) & 0xFFu
+                                                                 : (lastw ? first_new : (Rn & 0xFFu));
+                                    consts(R, U, D, right, pw, k + 1, s_c, sn_c, false, s_n, sn_n, dE0_n, dE1_n);
+                                } else {
+                                    const uint32_t right = (Rn >> 8) & 0xFFu;
+                                    consts(Rn, Un, Dn, right, nb0.y, 0, s_c, sn_c, false, s_n, sn_n, dE0_n, dE1_n);
+                                }
+                                const uint32_t o0 = (ap ? P1 : P0) + tab_s + 4u * (uint32_t)(dE0_n + 4);
+                                const uint32_t o1 = nP1 + tab_s + 4u * (uint32_t)(dE1_n + 4);
+                                A0n = TABLOAD(o0);
+                                A1n = TABLOAD(o1);
+                            }
+                            // 2. decision of this site
+                            const uint32_t A = ap ? A1 : A0;
+                            const bool acc = u < A;
+                            const int dE = ap ? dE1_c : dE0_c;
+                            bin += acc ? dE : 0;
+                            const uint32_t mask = 0xFFu << (8 * k);
+                            Rw = acc ? ((Rw & ~mask) | (sn_c << (8 * k))) : Rw;
+                            if (RECORD && acc) potts_count_move(cnt_lo, cnt_hi, s_c, sn_c);
+                            if (k == 0 && w == 0) first_new = acc ? sn_c : s_c;
+                            if (HIST) {
+                                if (HSMEM) {
+                                    if (active) red_shared(s_hist + bin, 1u);
+                                } else {
+                                    if (bin != run_bin) {
+                                        if (active)
+                                            atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]),
+                                                      (unsigned long long)run);
+                                        run_bin = bin;
+                                        run = 0;
+                                    }
+                                    ++run;
+                                }
+                            }
+                            // 3. state of the next site
+                            P0 = nP0;
+                            P1 = nP1;
+                            A0 = A0n;
+                            A1 = A1n;
+                            s_c = s_n;
+                            sn_c = sn_n;
+                            dE0_c = dE0_n;
+                            dE1_c = dE1_n;
+                            ap = acc;
+                        }
+                        loaded = !slot_last;
+                        if (slot_last && !lastw) {
+                            // next slot starts mid-row: its first site's left neighbour
+                            left0 = (R >> 24) & 0xFFu;
+                            left1 = (Rw >> 24) & 0xFFu;
+                            left1 = ap ? left1 : left0;
+                            left0 = left1;
+                        }
+                        LAT(kr + w) = Rw;
+                        R = Rn;
+                        U = Un;
+                        D = Dn;
+                    }
+                    if (it < total - kPottsRing) bar_arrive(kBarEmptyU + slot, NU);
+                }
+            }
+            if (RECORD && active) {
+                const int E = bin - 2 * V;
+                const int M = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
+                if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
+                if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
+                if (a.samples) {
+                    const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
+                    unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
+                    atomicAdd(&sp[bin], 1ull);
+                    atomicAdd(&sp[a.n_bins + bin], am);
+                    atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+                }
+            }
+        }
+        if (active) {
+            if (HIST && !HSMEM && run)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
+            if (!RECORD) {
+                uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int k = 0; k < a.lat_words; ++k) potts_count_word(LAT(k), cnt);
+                cnt_lo = cnt_hi = 0;
+                for (int k = 0; k < 4; ++k) {
+                    cnt_lo |= (uint64_t)cnt[k] << (16 * k);
+                    cnt_hi |= (uint64_t)cnt[k + 4] << (16 * k);
+                }
+            }
+            a.E[c] = bin - 2 * V;
+            a.M[c] = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
+            a.cnt[c] = cnt_lo;
+            a.cnt[a.p_pad + c] = cnt_hi;
+        }
+#undef TABLOAD
+        if (LSMEM)
+            for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
+#undef LAT
+    }
+    __syncthreads();
+    if (HIST && HSMEM) {
+        for (int i = tid; i < a.n_bins; i += NT) {
+            const uint32_t v = s_hist[i];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[i]), (unsigned long long)v);
+        }
+    }
+}
+
+__host__ __device__ constexpr size_t potts_ws_extra_smem() { return (size_t)kPottsRing * 16 * 32 * sizeof(uint4); }
+}  // namespace ws
+}  // namespace muca
