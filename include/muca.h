@@ -202,6 +202,50 @@ int muca_get_histogram(muca_ctx *ctx, uint64_t *H);
 int muca_get_samples(muca_ctx *ctx, uint64_t *n, uint64_t *sum_abs_m, uint64_t *sum_m2);
 int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
 
+/* ---------------------------------------------------------------------------
+ * Batched form (not in the paper): many independent lattices -- uneven L, both
+ * models -- advance together.  Each lattice is a full context (its own chains,
+ * weights, histogram) and follows exactly the trajectory it would follow alone
+ * (same random streams, same updates); only the scheduling differs:
+ *  - one persistent kernel sweeps every lattice's chains: work units of 32 chains,
+ *    longest first, taken from an atomic counter by a fixed grid;
+ *  - one launch updates every lattice's weights (Secs. 2-3), one rebuilds all
+ *    threshold tables;
+ *  - the whole loop of n_iterations can be captured once as a CUDA graph and
+ *    replayed with a single launch.
+ * ------------------------------------------------------------------------- */
+typedef struct muca_job {
+    int model, L, q, p; /* as muca_init */
+    uint64_t seed;
+} muca_job;
+
+typedef struct muca_batch muca_batch;
+
+/* Create n_jobs contexts (1 <= n_jobs <= 4096) sharing cfg and the stream (NULL:
+ * the batch creates its own non-blocking stream, needed for graph capture).
+ * Errors: as muca_init; MUCA_ERR_ARG for an empty job list. */
+int muca_batch_create(muca_batch **out, const muca_job *jobs, int n_jobs, const muca_config *cfg,
+                      void *cuda_stream);
+int muca_batch_destroy(muca_batch *b);
+
+/* n_iterations weight iterations of every lattice, each of n_sweeps sweeps per
+ * chain followed by the weight update (equivalent to muca_iterate +
+ * muca_update_weights on every context).  use_graph != 0 replays a captured CUDA
+ * graph (built once per (n_iterations, n_sweeps) and cached); returns when the work
+ * is queued.  Errors: MUCA_ERR_ARG, MUCA_ERR_CUDA. */
+int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_graph);
+
+/* The context of job j (owned by the batch; use it for state access). */
+muca_ctx *muca_batch_job(muca_batch *b, int j);
+
+/* Pick the persistent grid size, the lattice staging and the number of sweep
+ * launches per iteration by timing one iteration of n_sweeps on a scratch copy of
+ * the batch (the batch's own chains are not touched).  Results are cached in a JSON
+ * file keyed by the job list and the device name: cache_path, else the environment
+ * variable MUCA_AUTOTUNE_CACHE, else no cache.  *chosen (may be NULL) receives
+ * grid, staging (MUCA_STAGING_*) and launches per iteration. */
+int muca_batch_autotune(muca_batch *b, int n_sweeps, const char *cache_path, int chosen[3]);
+
 /* Checkpoint / resume: the complete state (spins, E, M, Potts counts, ln W, the
  * recursion accumulator, thresholds, counters, seed, production sums) in one file.
  * Philox is counter-based, so a resumed run continues bit-identically. */

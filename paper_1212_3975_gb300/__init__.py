@@ -12,7 +12,7 @@ import numpy as np
 from ._muca import (  # noqa: F401
     MUCA_BF16, MUCA_FP32, MUCA_FP64, MUCA_ISING, MUCA_POTTS, MUCA_RECURSION_ACCUMULATED,
     MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL, MUCA_STAGING_SHARED,
-    MucaConfig, MucaError, MucaIterStats, check, declared_symbols, lib)
+    MucaConfig, MucaError, MucaIterStats, MucaJob, check, declared_symbols, lib)
 
 PRECISIONS = {"fp64": MUCA_FP64, "fp32": MUCA_FP32, "bf16": MUCA_BF16}
 
@@ -55,9 +55,9 @@ class Muca:
 
     # -- lifecycle -------------------------------------------------------------
     def close(self):
-        if self._h:
+        if self._h and getattr(self, "_owned", True):
             lib().muca_destroy(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -189,3 +189,55 @@ class Muca:
         obj.L = int(round(V ** 0.5))
         obj.q = 2 if obj.model == 0 else 8
         return obj
+
+
+class MucaBatch:
+    """Many lattices advanced together: one persistent sweep kernel per iteration, a
+    batched weight update, optional CUDA-graph replay (a muca_batch)."""
+
+    def __init__(self, jobs, recursion=MUCA_RECURSION_ACCUMULATED, correction_width=0,
+                 staging=MUCA_STAGING_AUTO, stream=None):
+        arr = (MucaJob * len(jobs))(*[MucaJob(m, L, q, p, seed) for (m, L, q, p, seed) in jobs])
+        cfg = MucaConfig(recursion, correction_width, 0, staging)
+        self._h = ctypes.c_void_p()
+        check(lib().muca_batch_create(ctypes.byref(self._h), arr, len(jobs), ctypes.byref(cfg),
+                                      _ptr(stream)))
+        self.jobs = list(jobs)
+        self._views = []
+        for j, (m, L, q, p, _) in enumerate(jobs):
+            v = Muca.__new__(Muca)
+            v._h = ctypes.c_void_p(lib().muca_batch_job(self._h, j))
+            v._owned = False
+            v.model, v.L, v.q, v.p = m, L, q, p
+            v.n_bins = lib().muca_n_bins(v._h)
+            v.n_de = lib().muca_n_de(v._h)
+            v.V = L * L
+            self._views.append(v)
+
+    def job(self, j):
+        return self._views[j]
+
+    def __len__(self):
+        return len(self.jobs)
+
+    def iterate(self, n_iterations, n_sweeps, graph=True):
+        check(lib().muca_batch_iterate(self._h, n_iterations, n_sweeps, 1 if graph else 0))
+
+    def autotune(self, n_sweeps, cache_path=None):
+        chosen = (ctypes.c_int * 3)()
+        check(lib().muca_batch_autotune(self._h, n_sweeps,
+                                        cache_path.encode() if cache_path else None, chosen))
+        return tuple(chosen)
+
+    def close(self):
+        if self._h:
+            for v in self._views:
+                v._h = ctypes.c_void_p()
+            lib().muca_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

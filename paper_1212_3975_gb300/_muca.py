@@ -37,6 +37,11 @@ class MucaIterStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class MucaJob(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("L", ctypes.c_int), ("q", ctypes.c_int), ("p", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
 class MucaError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "error"), code, msg))
@@ -72,6 +77,12 @@ _SIGS = {
     "muca_get_energies": (ctypes.c_int, [_P, _P, _P]),
     "muca_get_histogram": (ctypes.c_int, [_P, _P]),
     "muca_get_samples": (ctypes.c_int, [_P, _P, _P, _P]),
+    "muca_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(MucaJob), ctypes.c_int,
+                                         ctypes.POINTER(MucaConfig), _P]),
+    "muca_batch_destroy": (ctypes.c_int, [_P]),
+    "muca_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "muca_batch_job": (_P, [_P, ctypes.c_int]),
+    "muca_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
     "muca_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "muca_load": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_char_p, _P]),
 }

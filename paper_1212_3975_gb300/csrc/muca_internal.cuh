@@ -102,6 +102,23 @@ struct SweepPlan {
     size_t smem_bytes;
 };
 
+// Device view of one lattice of a batch (pointers into its context).
+struct BatchJob {
+    int model, L, q, p, p_pad, row_words, lat_words, n_bins, n_de, V;
+    int accumulated, width;
+    uint32_t key0, ctr3_iter;   // seed low word; counter word 3 of weight iterations
+    uint32_t *lat;
+    int32_t *E, *M;
+    uint64_t *cnt;
+    double *lnw, *P, *wscratch;
+    uint8_t *acc;
+    uint32_t *thr, *ktab;
+    uint64_t *H;
+    muca_iter_stats *stats;
+    uint32_t *iteration;        // device counter of weight iterations (counter word 2)
+    int flags;                  // staging of the sweep body: 4 table, 2 histogram, 1 lattice in smem
+};
+
 }  // namespace muca
 
 // Host-side context (opaque to callers).
@@ -167,6 +184,7 @@ int launch_stats(muca_ctx *ctx);
 int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision,
                     double *d_out /* [4][n_beta] */);
 SweepPlan plan_sweeps(const muca_ctx *ctx);
+cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st);
 int launch_ktab(muca_ctx *ctx);
 size_t ws_extra_smem(int model);
 cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,

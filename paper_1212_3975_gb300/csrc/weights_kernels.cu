@@ -54,9 +54,9 @@ struct BlockStats {
 //   4. boundary correction beyond [lo, hi] with the slope of the innermost
 //      `width` bins (Sec. 3);
 //   5. ln W -= max over accessible bins; inaccessible bins = 0.
-__global__ void __launch_bounds__(1024) update_kernel(double *lnw, double *P, double *scratch, const uint64_t *H,
-                                                      const uint8_t *acc, int n_bins, int accumulated,
-                                                      int width_cfg, muca_iter_stats *stats)
+__device__ __forceinline__ void update_body(double *lnw, double *P, double *scratch, const uint64_t *H,
+                                            const uint8_t *acc, int n_bins, int accumulated, int width_cfg,
+                                            muca_iter_stats *stats)
 {
     __shared__ unsigned long long s_total[32], s_min[32], s_max[32], s_ns[32], s_K[32];
     __shared__ int s_lo[32], s_hi[32];
@@ -205,7 +205,54 @@ __global__ void __launch_bounds__(1024) update_kernel(double *lnw, double *P, do
     for (int b = tid; b < n_bins; b += blockDim.x) lnw[b] = acc[b] ? __dsub_rn(lnw[b], top) : 0.0;
 }
 
+__global__ void __launch_bounds__(1024) update_kernel(double *lnw, double *P, double *scratch, const uint64_t *H,
+                                                      const uint8_t *acc, int n_bins, int accumulated,
+                                                      int width_cfg, muca_iter_stats *stats)
+{
+    update_body(lnw, P, scratch, H, acc, n_bins, accumulated, width_cfg, stats);
+}
+
+// one block per lattice of a batch
+__global__ void __launch_bounds__(1024) update_batch_kernel(const BatchJob *jobs)
+{
+    const BatchJob &j = jobs[blockIdx.x];
+    update_body(j.lnw, j.P, j.wscratch, j.H, j.acc, j.n_bins, j.accumulated, j.width, j.stats);
+}
+
+// thresholds of every lattice of a batch: blockIdx.y = lattice
+__global__ void thresholds_batch_kernel(const BatchJob *jobs)
+{
+    const BatchJob &j = jobs[blockIdx.y];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < j.n_bins * j.n_de; t += gridDim.x * blockDim.x) {
+        const int b = t / j.n_de, col = t % j.n_de;
+        const int bp = b + bin_delta(j.model, col);
+        uint32_t A = 0u;
+        if (j.acc[b] && bp >= 0 && bp < j.n_bins && j.acc[bp]) {
+            const double d = __dsub_rn(j.lnw[bp], j.lnw[b]);
+            if (d >= 0.0) {
+                A = kAlways;
+            } else {
+                const double x = floor(ldexp(exp(d), 32));
+                A = x >= 4294967295.0 ? kAlways : (uint32_t)x;
+            }
+        }
+        j.thr[t] = A;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st)
+{
+    update_batch_kernel<<<n_jobs, 1024, 0, st>>>(d_jobs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((max_thr + 255) / 256, n_jobs);
+    thresholds_batch_kernel<<<grid, 256, 0, st>>>(d_jobs);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) note_launches(2);
+    return e;
+}
 
 int launch_thresholds(muca_ctx *ctx)
 {
