@@ -211,13 +211,20 @@ def run_gpu(args):
     achieved = inst_per_attempt * att_per_launch / (sweep_avg_ms * 1e-3) / 1e9   # Gwarp-inst/s
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 4 * sm_max * 1e6 / 1e9
+    # the launch has p/32 blocks of 4 warps, one warp per scheduler it occupies
+    occupied = min(608, (w["p"] + 31) // 32 * 4)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-        "frac": achieved / peak, "traffic": None,
-        "kernel": "ising_sweep_kernel (weight-iteration sweeps)",
+        "frac": achieved / peak,
+        "traffic": TRAFFIC_BYTES_PER_LAUNCH_ISING_L64,
+        "kernel": "ising_ws_kernel (weight-iteration sweeps, warp-specialised)",
         "launch_ms": sweep_avg_ms,
         "attempts_per_ns": att_per_launch / (sweep_avg_ms * 1e6),
-        "peak_note": "152 SMs x 4 schedulers x 1 warp-instruction/clock at %.0f MHz" % sm_max,
+        "warp_inst_per_attempt": inst_per_attempt,
+        "peak_note": "152 SMs x 4 schedulers x 1 warp-instruction/clock at %.0f MHz, of measured "
+                     "max clock" % sm_max,
+        "occupied_schedulers": occupied,
+        "frac_of_occupied_schedulers": achieved / (peak * occupied / 608.0),
     }
     result = {
         "metric": METRIC, "value": value, "unit": "attempts/ns", "n_gpus": world,
@@ -242,7 +249,13 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_sample(w, seconds_hint=True)
-    g.close()
+    if rank == 0 and not args.no_extras:
+        with torch.cuda.stream(stream):
+            result["reweight"] = reweight_rates(m, g, torch, stream, betas_h, betas_d)
+        g.close()
+        result["batched"] = batched_comparison(m, torch)
+    else:
+        g.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -250,13 +263,110 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def reweight_rates(m, g, torch, stream, betas_h, betas_d):
+    """Reweighted betas per second of muca_reweight in FP64 and FP32 on the
+    production sums of the last step, and the FP32 error per observable."""
+    n_beta = len(betas_h)
+    out = {}
+    res = {}
+    for name, prec in (("fp64", m.MUCA_FP64), ("fp32", m.MUCA_FP32)):
+        o = torch.empty((4, n_beta), dtype=torch.float64, device="cuda")
+        g.reweight(betas_d, prec, out=o)          # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            g.reweight(betas_d, prec, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name + "_betas_per_s"] = n_beta / (ms * 1e-3)
+        out[name + "_ms"] = ms
+        res[name] = o.cpu().numpy()
+    err = np.abs(res["fp32"] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
+    out["fp32_max_rel_err"] = {k: float(err[i].max()) for i, k in enumerate(("e", "C", "absm", "chi"))}
+    out["fp32_within_1e-6"] = bool(err.max() <= 1e-6)
+    out["n_beta"] = n_beta
+    out["n_bins"] = g.n_bins
+    return out
+
+
+def batched_comparison(m, torch):
+    """Mixed workload (Ising L = 16..128 and 8-Potts L = 16..48, 256 chains each,
+    20 x 200 sweeps): one persistent launch per iteration under a CUDA graph,
+    autotuned, against one launch sequence per lattice."""
+    wb = workloads.BATCHED_MIXED
+    jobs, iters, sweeps = wb["jobs"], wb["iterations"], wb["sweeps"]
+    att = sum(p * L * L for (_, L, _, p, _) in jobs) * iters * sweeps
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    ctxs = [m.Muca(*j) for j in jobs]
+
+    def per_lattice():
+        for c in ctxs:
+            for _ in range(iters):
+                m.check(m.lib().muca_iterate(c.handle, sweeps, None))
+                m.check(m.lib().muca_update_weights(c.handle, None))
+
+    t_seq = timed(per_lattice)
+    for c in ctxs:
+        c.close()
+    b = m.MucaBatch(jobs)
+    choice = b.autotune(sweeps)
+    b.iterate(1, sweeps, graph=True)        # builds the 1-iteration graph (warm-up)
+    t_bat = timed(lambda: b.iterate(iters, sweeps, graph=True))
+    b.close()
+    return {"workload": "mixed: Ising L=16..128 + 8-Potts L=16..48, 256 chains each, %d x %d sweeps"
+                        % (iters, sweeps),
+            "per_lattice_attempts_per_ns": att / t_seq / 1e9,
+            "batched_attempts_per_ns": att / t_bat / 1e9,
+            "speedup": t_seq / t_bat, "per_lattice_s": t_seq, "batched_s": t_bat,
+            "autotuned": {"grid": choice[0], "staging": choice[1], "launches_per_iteration": choice[2]}}
+
+
 # measured with ncu (inst_executed / attempts) on the weight-iteration sweep kernel of
 # the 64x64 Ising workload; see profiles/
-INST_PER_ATTEMPT_ISING_L64 = 50.0 / 32.0
+INST_PER_ATTEMPT_ISING_L64 = 2.02
+# dram__bytes_read.sum + dram__bytes_write.sum of one weight-iteration launch of the same
+# kernel (staging of table, histogram and lattices only; independent of the sweep count)
+TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = 671744
+
+
+def run_probe(args):
+    """One small launch of a workload's weight-iteration sweeps, for profiler captures:
+    start, a 2-sweep iteration and update (the launch skipped by -s 1), then one
+    iteration of --probe-sweeps sweeps (the captured launch)."""
+    import torch
+    import paper_1212_3975_gb300 as m
+    from paper_1212_3975_gb300 import build as b
+    b.build()
+    w = workloads.WORKLOADS[args.probe]
+    g = m.Muca(w["model"], w["L"], w["q"], w["p"], w["seed"])
+    if w.get("fixed_beta"):
+        lnw = workloads.canonical_lnw(w["model"], w["L"], w["fixed_beta"])
+        g.set_lnw(lnw - lnw.max())
+    g.iterate(2)
+    g.update_weights()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.iterate(args.probe_sweeps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"probe": args.probe, "sweeps": args.probe_sweeps,
+                      "attempts_per_ns": w["p"] * w["L"] * w["L"] * args.probe_sweeps / dt / 1e9}))
+    g.close()
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_sample(w, seconds_hint=False, it_sweeps=400, prod_sweeps=100):
+def cpu_sample(w, seconds_hint=False, it_sweeps=2000, prod_sweeps=500):
     """The oracle as it stands on the host cores, on a bounded sample of the workload:
     all p chains, one weight iteration of `it_sweeps` sweeps, the update, a production
     run of `prod_sweeps` sweeps and the FP64 reweighting to every beta."""
@@ -313,7 +423,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the reweighting and batched lines")
+    ap.add_argument("--probe", default=None, choices=sorted(workloads.WORKLOADS),
+                    help="run one small sweep launch of a workload (for profiler captures)")
+    ap.add_argument("--probe-sweeps", type=int, default=10)
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args)
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
