@@ -50,6 +50,22 @@ def workload_attempts(w):
     return w["p"] * V * (w["iterations"] * w["sweeps"] + w["production"])
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the time)."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(attempts_per_rank, world, seconds):
+    """Attempts per nanosecond of the whole job: every rank ran its own replica."""
+    return attempts_per_rank * world / (seconds * 1e9)
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     def __init__(self, index):
@@ -192,15 +208,10 @@ def run_gpu(args):
         barrier()
         e2e_s = time.perf_counter() - h0
 
-    total_ms = elapsed_ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
+    total_ms, e2e_s = max_over_ranks([elapsed_ms, e2e_s], world, "cuda")
     attempts = workload_attempts(w)
-    value = attempts * args.steps * world / (total_ms * 1e6)
-    e2e_value = attempts * e2e_steps * world / (e2e_s * 1e9)
+    value = whole_job_rate(attempts * args.steps, world, total_ms * 1e-3)
+    e2e_value = whole_job_rate(attempts * e2e_steps, world, e2e_s)
 
     # roofline of the dominant kernel (sweeps of the weight iterations)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
@@ -269,7 +280,7 @@ def reweight_rates(m, g, torch, stream, betas_h, betas_d):
     n_beta = len(betas_h)
     out = {}
     res = {}
-    for name, prec in (("fp64", m.MUCA_FP64), ("fp32", m.MUCA_FP32)):
+    for name, prec in (("fp64", m.MUCA_FP64), ("fp32", m.MUCA_FP32), ("bf16", m.MUCA_BF16)):
         o = torch.empty((4, n_beta), dtype=torch.float64, device="cuda")
         g.reweight(betas_d, prec, out=o)          # warm-up
         torch.cuda.synchronize()
@@ -285,9 +296,10 @@ def reweight_rates(m, g, torch, stream, betas_h, betas_d):
         out[name + "_betas_per_s"] = n_beta / (ms * 1e-3)
         out[name + "_ms"] = ms
         res[name] = o.cpu().numpy()
-    err = np.abs(res["fp32"] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
-    out["fp32_max_rel_err"] = {k: float(err[i].max()) for i, k in enumerate(("e", "C", "absm", "chi"))}
-    out["fp32_within_1e-6"] = bool(err.max() <= 1e-6)
+    for name in ("fp32", "bf16"):
+        err = np.abs(res[name] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
+        out[name + "_max_rel_err"] = {k: float(err[i].max()) for i, k in enumerate(("e", "C", "absm", "chi"))}
+        out[name + "_within_1e-6"] = bool(err.max() <= 1e-6)
     out["n_beta"] = n_beta
     out["n_bins"] = g.n_bins
     return out

@@ -18,6 +18,8 @@
 //            large numbers cancel in FP32, and the contraction uses centred columns
 //            {1, dE, dE^2, d|m|, d|m|^2, var_b(|m|)} so that C and chi do not suffer
 //            from cancellation.  Sums are combined across threads in FP64.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -282,6 +284,169 @@ __global__ void __launch_bounds__(256) reweight_fp32_kernel(BinData d, const dou
     }
 }
 
+// ------------------------------ BF16 tensor cores ------------------------------
+// Tile of 16 betas = the M dimension of mma.m16n8k16; 16 bins per K step; the 6
+// centred observable columns (padded to 8) are N.  Table entries and columns are
+// split as x = x_hi + x_lo (two BF16 values) and multiplied as hi*hi + hi*lo + lo*hi
+// with FP32 accumulation.  The FP64 prologue (reference bin, window, per-beta
+// shifts) is the one of the FP32 form.
+template <int TILE>
+__device__ void tile_prologue(const BinData &d, const double *betas, int n_beta, int n_bins, int j0, int nt,
+                              double *s_val, int *s_idx, float *s_c, float *s_db, double &lnOT, double &ET,
+                              double &x1T, double &betaT, int &lo, int &hi)
+{
+    betaT = betas[j0 + nt / 2];
+    double best = -INFINITY;
+    int kT = n_bins;
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+        const double l = d.lnO[b];
+        if (l == -INFINITY) continue;
+        const double a = __dsub_rn(l, __dmul_rn(betaT, d.E[b]));
+        if (a > best || (a == best && b < kT)) { best = a; kT = b; }
+    }
+    block_argmax(best, kT, s_val, s_idx);
+    lnOT = d.lnO[kT];
+    ET = d.E[kT];
+    x1T = d.x1[kT];
+    double dbmax = 0.0;
+    for (int t = 0; t < nt; ++t) dbmax = fmax(dbmax, fabs(betas[j0 + t] - betaT));
+    lo = n_bins;
+    hi = -1;
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+        const double l = d.lnO[b];
+        if (l == -INFINITY) continue;
+        const double dE = d.E[b] - ET;
+        const double G = (l - lnOT) - betaT * dE;
+        if (G + dbmax * fabs(dE) >= kCut) { lo = min(lo, b); hi = max(hi, b); }
+    }
+    double v1 = -(double)lo;
+    int i1 = 0;
+    block_argmax(v1, i1, s_val, s_idx);
+    lo = (int)(-v1);
+    double v2 = (double)hi;
+    int i2 = 0;
+    block_argmax(v2, i2, s_val, s_idx);
+    hi = (int)v2;
+    for (int t = 0; t < TILE; ++t) {
+        if (t >= nt) {
+            if (threadIdx.x == 0) { s_c[t] = -1e30f; s_db[t] = 0.f; }
+            continue;
+        }
+        const double beta = betas[j0 + t];
+        double m = -INFINITY;
+        int mi = n_bins;
+        for (int b = lo + (int)threadIdx.x; b <= hi; b += blockDim.x) {
+            const double l = d.lnO[b];
+            if (l == -INFINITY) continue;
+            const double a = __dsub_rn(l, __dmul_rn(beta, d.E[b]));
+            if (a > m || (a == m && b < mi)) { m = a; mi = b; }
+        }
+        block_argmax(m, mi, s_val, s_idx);
+        if (threadIdx.x == 0) {
+            s_c[t] = (float)(((lnOT - beta * ET) - m) * kLog2e);
+            s_db[t] = (float)((beta - betaT) * kLog2e);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float first, float second)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(first, second);  // .x (low half) = first
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) reweight_bf16_kernel(BinData d, const double *betas, int n_beta, int n_bins,
+                                                            int V, double mnorm, Observables o)
+{
+    constexpr int TILE = 16;
+    __shared__ double s_val[32 * 6];
+    __shared__ int s_idx[32];
+    __shared__ float s_c[TILE], s_db[TILE];
+    __shared__ double s_red[4][TILE][8];
+    const int j0 = blockIdx.x * TILE;
+    const int nt = min(TILE, n_beta - j0);
+    double lnOT, ET, x1T, betaT;
+    int lo, hi;
+    tile_prologue<TILE>(d, betas, n_beta, n_bins, j0, nt, s_val, s_idx, s_c, s_db, lnOT, ET, x1T, betaT, lo, hi);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;          // fragment coordinates
+    const float c0 = s_c[g], db0 = s_db[g], c1 = s_c[g + 8], db1 = s_db[g + 8];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int base = lo + 16 * warp; base <= hi; base += 64) {
+        // each lane prepares one bin of the chunk (lanes 16..31 repeat lanes 0..15)
+        const int b = base + (lane & 15);
+        float G = -1e30f, dE = 0.f, dx = 0.f, vb = 0.f;
+        if (b <= hi) {
+            const double l = d.lnO[b];
+            if (l != -INFINITY) {
+                const double dEd = d.E[b] - ET;
+                G = (float)(((l - lnOT) - betaT * dEd) * kLog2e);
+                dE = (float)dEd;
+                dx = (float)(d.x1[b] - x1T);
+                vb = (float)d.v[b];
+            }
+        }
+        float x[2][4], col[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 2 * t4 + (q & 1) + 8 * (q >> 1);  // bin of the chunk held by this thread
+            const float Gq = __shfl_sync(0xffffffffu, G, k);
+            const float dEq = __shfl_sync(0xffffffffu, dE, k);
+            const float dxq = __shfl_sync(0xffffffffu, dx, k);
+            const float vq = __shfl_sync(0xffffffffu, vb, k);
+            x[0][q] = exp2f(fmaf(-db0, dEq, Gq + c0));
+            x[1][q] = exp2f(fmaf(-db1, dEq, Gq + c1));
+            const float cv = g == 0 ? 1.f : g == 1 ? dEq : g == 2 ? dEq * dEq : g == 3 ? dxq : g == 4 ? dxq * dxq
+                                                                                 : g == 5 ? vq : 0.f;
+            col[q] = Gq > -1e29f ? cv : 0.f;
+        }
+        uint32_t ah[4], al[4], bh[2], bl[2];
+        // A registers: {row g, bins q0,q1}, {row g+8, q0,q1}, {row g, q2,q3}, {row g+8, q2,q3}
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int row = r & 1, qp = (r >> 1) * 2;
+            const float h0 = bf16_round(x[row][qp]), h1 = bf16_round(x[row][qp + 1]);
+            ah[r] = pack_bf16x2(h0, h1);
+            al[r] = pack_bf16x2(x[row][qp] - h0, x[row][qp + 1] - h1);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float h0 = bf16_round(col[2 * r]), h1 = bf16_round(col[2 * r + 1]);
+            bh[r] = pack_bf16x2(h0, h1);
+            bl[r] = pack_bf16x2(col[2 * r] - h0, col[2 * r + 1] - h1);
+        }
+        mma_bf16_16816(acc, ah, bh);
+        mma_bf16_16816(acc, ah, bl);
+        mma_bf16_16816(acc, al, bh);
+    }
+    // accumulators: (row g, cols 2t4, 2t4+1), (row g+8, cols 2t4, 2t4+1)
+    s_red[warp][g][2 * t4] = acc[0];
+    s_red[warp][g][2 * t4 + 1] = acc[1];
+    s_red[warp][g + 8][2 * t4] = acc[2];
+    s_red[warp][g + 8][2 * t4 + 1] = acc[3];
+    __syncthreads();
+    if ((int)threadIdx.x < nt) {
+        const int t = threadIdx.x;
+        double S[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < 4; ++w)
+            for (int k = 0; k < 6; ++k) S[k] += s_red[w][t][k];
+        write_obs(o, j0 + t, betas[j0 + t], ET, x1T, S[0], S[1], S[2], S[3], S[4], S[5], V, mnorm);
+    }
+}
+
 }  // namespace
 
 // Same kernels with every buffer supplied by the caller: per-bin scratch of
@@ -325,8 +490,11 @@ int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precis
     } else if (precision == MUCA_FP32) {
         const int tiles = (n_beta + 7) / 8;
         reweight_fp32_kernel<8><<<tiles, 256, 0, ctx->stream>>>(d, d_betas, n_beta, ctx->n_bins, ctx->V, mnorm, o);
+    } else if (precision == MUCA_BF16) {
+        const int tiles = (n_beta + 15) / 16;
+        reweight_bf16_kernel<<<tiles, 128, 0, ctx->stream>>>(d, d_betas, n_beta, ctx->n_bins, ctx->V, mnorm, o);
     } else {
-        return fail(MUCA_ERR_ARG, "precision must be MUCA_FP64 or MUCA_FP32");
+        return fail(MUCA_ERR_ARG, "precision must be MUCA_FP64, MUCA_FP32 or MUCA_BF16");
     }
     MUCA_CUDA_TRY(cudaGetLastError());
     note_launches(1);

@@ -306,3 +306,28 @@ def test_errors_and_state(muca):
         muca.Muca.load("/nonexistent/ck.bin")
     assert ei.value.code == muca._muca.MUCA_ERR_IO
     g.close()
+
+
+@pytest.mark.parametrize("model,L,p,sweeps", [(ISING, 16, 64, 200), (POTTS, 12, 64, 200),
+                                              (ISING, 96, 256, 40)])
+def test_reweight_precisions_against_oracle(muca, model, L, p, sweeps):
+    """FP64 / FP32 / BF16 tensor-core reweighting against the oracle's FP64 binned form:
+    FP64 within 1e-10, FP32 within 1e-6 (the bar of the reweighting metric), BF16 with
+    its error measured and bounded (hi/lo split products, FP32 accumulation)."""
+    q = 2 if model == ISING else 8
+    beta = 0.42 if model == ISING else 1.33
+    lnw = random_weights(model, L, 13, beta)
+    betas = np.linspace(beta - 0.06, beta + 0.06, 203)
+    with muca.Muca(model, L, q, p, 17) as g:
+        g.set_lnw(lnw)
+        g.thermalize(20)
+        E_rec, M_rec = g.produce(sweeps)
+        res = {prec: g.reweight(betas, prec) for prec in ("fp64", "fp32", "bf16")}
+        lnw_g = g.get_lnw()
+    ref = reweight.reweight_binned(model, L, q, lnw_g,
+                                   *reweight.bin_series(model, L, E_rec, M_rec), betas)
+    bounds = {"fp64": 1e-10, "fp32": 1e-6, "bf16": 2e-3}
+    for prec, r in res.items():
+        for k in ("e", "C", "absm", "chi"):
+            rel = np.abs(r[k] - ref[k]) / np.maximum(np.abs(ref[k]), 1e-300)
+            assert rel.max() <= bounds[prec], (prec, k, rel.max())
