@@ -222,11 +222,15 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                                                                       reinterpret_cast<const char *>(a.ktab) + P0 + K0 - tab_s));
                         uint32_t A1 = TSMEM ? lds_u32(P1 + K1) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
                                                                       reinterpret_cast<const char *>(a.ktab) + P1 + K1 - tab_s));
-                        uint4 blk = src[0];
+                        // draws of the word: group g+1 is loaded while group g is decided
+                        uint4 blk = src[0], blk_next = src[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int k = j & 3;
-                            if (k == 0 && j > 0) blk = src[(j >> 2) * 32];
+                            if (k == 0 && j > 0) {
+                                blk = blk_next;
+                                if (j < 28) blk_next = src[((j >> 2) + 1) * 32];
+                            }
                             const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
                             // Issue order matters (a warp issues in order): first the loads
                             // of site j+1, whose offsets need only the previous decision,
