@@ -75,6 +75,182 @@ struct Snap {
     uint32_t pad[3];
 };
 
+// Neighbour planes of one row word: lo/hi = bit-sliced count of the unequal up, down
+// and right neighbours, qw = site differs from its old left neighbour.
+struct WordCtx {
+    uint32_t R, Rn;        // the word and its right neighbour word (old values)
+    uint32_t ua, ub, tr;   // unequal up / down / right
+    uint32_t lo, hi, qw;
+};
+
+__device__ __forceinline__ WordCtx word_ctx(uint32_t R, uint32_t U, uint32_t D, uint32_t Rn, uint32_t lbit)
+{
+    WordCtx x;
+    x.R = R;
+    x.Rn = Rn;
+    x.ua = R ^ U;
+    x.ub = R ^ D;
+    x.tr = R ^ ((R >> 1) | ((Rn & 1u) << 31));
+    x.lo = x.ua ^ x.ub ^ x.tr;
+    x.hi = (x.ua & x.ub) | (x.tr & (x.ua ^ x.ub));
+    x.qw = R ^ ((R << 1) | lbit);
+    return x;
+}
+
+// Ising decider for rows of whole words (L % 32 == 0, at least two words per row).
+// The sites of consecutive words form one software pipeline: while word it is decided,
+// the lattice words and neighbour planes of word it+1 are prepared, its first draws
+// are loaded (site 28) and the candidate thresholds of its site 0 are loaded with the
+// offsets resolved by site 30's decision (site 31), exactly as between sites of one
+// word.  (With one word per row the next word's upper neighbours are this word's new
+// spins, so that case keeps the per-word form.)
+template <bool BOOK, bool TSMEM, int RU, int RS>
+__device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t *lp, const size_t ls,
+                                                    const uint32_t tab_s, const uint4 *s_ring, Snap *s_snap,
+                                                    const int NU, const int lane, const int total, uint32_t &bin20,
+                                                    uint32_t &d20p, bool &ap)
+{
+#define LAT(k) lp[(size_t)(k) * ls]
+    const int L = a.L, RW = a.row_words;
+    auto tload = [&](uint32_t o) -> uint32_t {
+        return TSMEM ? lds_u32(o)
+                     : ldg_nc_u32(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + o - tab_s));
+    };
+    auto row_up = [&](int y) { return (y == 0 ? L - 1 : y - 1) * RW; };    // row above: updated
+    auto row_down = [&](int y) { return (y == L - 1 ? 0 : y + 1) * RW; };  // row below: old (new for y = L-1)
+    // constants of site j of a word: table addresses for the previous attempt rejected /
+    // accepted (left neighbour old / flipped) and the bin changes (x 20 bytes) if accepted
+    auto consts = [&](const WordCtx &x, int j, bool rowstart, bool rowend, uint32_t first_new, uint32_t &K0,
+                      uint32_t &K1, uint32_t &D0, uint32_t &D1) {
+        uint32_t pre = ((x.lo >> j) & 1u) + ((x.hi >> j) & 1u) * 2u;
+        if (j == 31) {
+            // row end: the right neighbour is site 0 of the row, already updated
+            const uint32_t pre_end = ((x.ua >> 31) & 1u) + ((x.ub >> 31) & 1u) + ((x.R >> 31) ^ first_new);
+            pre = rowend ? pre_end : pre;
+        }
+        const uint32_t q = (x.qw >> j) & 1u;
+        const uint32_t n0 = pre + q;
+        const uint32_t n1 = (j == 0 && rowstart) ? n0 : pre + 1u - q;
+        K0 = tab_s + 4u * n0;
+        K1 = tab_s + 4u * n1;
+        D0 = 40u - 20u * n0;
+        D1 = 40u - 20u * n1;
+    };
+
+    // ---- word 0
+    int y = 0, w = 0;
+    WordCtx cur = word_ctx(LAT(0), LAT(row_up(0)), LAT(row_down(0)), LAT(1), (LAT(RW - 1) >> 31) & 1u);
+    uint32_t first_new = 0u;
+    uint32_t P0 = bin20, P1 = bin20 + d20p;
+    uint32_t K0, K1, D0, D1;
+    consts(cur, 0, true, false, 0u, K0, K1, D0, D1);
+    uint32_t A0 = tload(P0 + K0), A1 = tload(P1 + K1);
+    bar_sync(kBarFullU + 0, NU);
+    uint4 blk = s_ring[lane], blk_next = s_ring[32 + lane];
+
+    for (int it = 0; it < total; ++it) {
+        const bool lastw = (w == RW - 1);
+        const bool has_next = it + 1 < total;
+        const int slot = it % RU;
+        const uint4 *src = s_ring + slot * 8 * 32 + lane;
+        // next word: (y1, w1)
+        int y1 = y, w1 = w + 1;
+        if (w1 == RW) {
+            w1 = 0;
+            y1 = (y + 1 == L) ? 0 : y + 1;
+        }
+        const int slot1 = (it + 1) % RU;
+        const uint4 *src1 = s_ring + slot1 * 8 * 32 + lane;
+        // its lattice words: all old, except the row above (finished: at least two words
+        // per row) and, for the last row, the row below (row 0, finished)
+        uint32_t R1 = 0u, U1 = 0u, D1w = 0u, Rn1 = 0u, lb1 = 0u;
+        if (has_next) {
+            const int kr1 = y1 * RW;
+            R1 = (w1 == 0) ? LAT(kr1) : cur.Rn;
+            U1 = LAT(row_up(y1) + w1);
+            D1w = LAT(row_down(y1) + w1);
+            Rn1 = (w1 + 1 < RW) ? LAT(kr1 + w1 + 1) : 0u;
+            lb1 = (w1 == 0) ? ((LAT(kr1 + RW - 1) >> 31) & 1u) : (cur.R >> 31);
+        }
+        WordCtx nx;
+        uint4 nblk = make_uint4(0u, 0u, 0u, 0u), nblk_next = nblk;
+        uint32_t Rw = cur.R;
+        uint32_t K0n = 0u, K1n = 0u, D0n = 0u, D1n = 0u;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int k = j & 3;
+            if (k == 0 && j > 0) {
+                blk = blk_next;
+                if (j < 28) blk_next = src[((j >> 2) + 1) * 32];
+            }
+            if (j == 8) nx = word_ctx(R1, U1, D1w, Rn1, lb1);
+            if (j == 28 && has_next) {
+                // first draws of the next word
+                bar_sync(kBarFullU + slot1, NU);
+                nblk = src1[0];
+                nblk_next = src1[32];
+            }
+            const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
+            // loads of the next site first (offsets resolved by the previous decision),
+            // then the decision of this site
+            uint32_t A0n = 0u, A1n = 0u;
+            const bool more = (j < 31) || has_next;
+            if (more) {
+                if (j < 31)
+                    consts(cur, j + 1, w == 0, lastw, first_new, K0n, K1n, D0n, D1n);
+                else
+                    consts(nx, 0, w1 == 0, false, 0u, K0n, K1n, D0n, D1n);
+                const uint32_t o0 = ap ? P1 + K0n : P0 + K0n;
+                const uint32_t o1 = ap ? P1 + D1 + K1n : P0 + D0 + K1n;
+                A0n = tload(o0);
+                A1n = tload(o1);
+            }
+            const uint32_t A = ap ? A1 : A0;
+            const bool acc = u < A;
+            const uint32_t nP0 = ap ? P1 : P0;
+            const uint32_t nP1 = ap ? P1 + D1 : P0 + D0;
+            A0 = A0n;
+            A1 = A1n;
+            P0 = nP0;
+            P1 = nP1;
+            D0 = D0n;
+            D1 = D1n;
+            Rw ^= acc ? (1u << j) : 0u;
+            if (j == 0 && w == 0) first_new = (cur.R & 1u) ^ (acc ? 1u : 0u);
+            ap = acc;
+        }
+        if (it < total - RU) bar_arrive(kBarEmptyU + slot, NU);
+        LAT(y * RW + w) = Rw;
+        if (BOOK) {
+            uint32_t lo = cur.lo, hi = cur.hi;
+            if (lastw) {
+                // the row's last site saw the updated site 0 as its right neighbour
+                const uint32_t tr2 = (cur.tr & 0x7FFFFFFFu) | (((cur.R >> 31) ^ first_new) << 31);
+                lo = cur.ua ^ cur.ub ^ tr2;
+                hi = (cur.ua & cur.ub) | (tr2 & (cur.ua ^ cur.ub));
+            }
+            const int ss = it % RS;
+            if (it >= RS) bar_sync(kBarEmptyS + ss, 64);
+            Snap *sn = s_snap + ss * 32 + lane;
+            sn->lo = lo;
+            sn->hi = hi;
+            sn->qw = cur.qw;
+            sn->flip = cur.R ^ Rw;
+            sn->rold = cur.R;
+            bar_arrive(kBarFullS + ss, 64);
+        }
+        if (lastw) first_new = 0u;
+        cur = nx;
+        blk = nblk;
+        blk_next = nblk_next;
+        y = y1;
+        w = w1;
+    }
+    bin20 = P0;
+    d20p = P1 - P0;
+#undef LAT
+}
+
 template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
 __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
@@ -165,6 +341,10 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         uint32_t bin20 = 20u * (uint32_t)bin0;  // 4*5*bin before the previous decision
         uint32_t d20p = 0u;                     // its change if the previous attempt was accepted
         bool ap = false;                        // previous attempt accepted
+        if (last_bits == 32 && RW >= 2) {
+            ising_decide_stream<BOOK, TSMEM, kRingU, kRingS>(a, lp, ls, tab_s, s_ring, s_snap, NU, lane, total, bin20,
+                                                             d20p, ap);
+        } else {
         int it = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             for (int y = 0; y < L; ++y) {
@@ -324,6 +504,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                     D = Dn;
                 }
             }
+        }
         }
         if (active && !BOOK) {
             // no bookkeeper: apply the pending decision and recount M
