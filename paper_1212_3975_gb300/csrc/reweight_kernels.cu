@@ -287,9 +287,12 @@ __global__ void __launch_bounds__(256) reweight_fp32_kernel(BinData d, const dou
 // ------------------------------ BF16 tensor cores ------------------------------
 // Tile of 16 betas = the M dimension of mma.m16n8k16; 16 bins per K step; the 6
 // centred observable columns (padded to 8) are N.  Table entries and columns are
-// split as x = x_hi + x_lo (two BF16 values) and multiplied as hi*hi + hi*lo + lo*hi
-// with FP32 accumulation.  The FP64 prologue (reference bin, window, per-beta
-// shifts) is the one of the FP32 form.
+// split into three BF16 terms, x = x_h + x_m + x_l (residual below 2^-26 |x|), and
+// multiplied as the six products of order <= 2 (hh, hm, mh, hl, lh, mm; the dropped
+// ones are below 2^-24 relative); each chunk's six products are accumulated by the
+// tensor cores in FP32 from zero (their FP32 accumulation need not round to nearest)
+// and added to FP64 registers.  The FP64 prologue (reference bin, window, per-beta shifts) is the one of
+// the FP32 form.
 template <int TILE>
 __device__ void tile_prologue(const BinData &d, const double *betas, int n_beta, int n_bins, int j0, int nt,
                               double *s_val, int *s_idx, float *s_c, float *s_db, double &lnOT, double &ET,
@@ -385,6 +388,7 @@ __global__ void __launch_bounds__(128) reweight_bf16_kernel(BinData d, const dou
     const int g = lane >> 2, t4 = lane & 3;          // fragment coordinates
     const float c0 = s_c[g], db0 = s_db[g], c1 = s_c[g + 8], db1 = s_db[g + 8];
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    double accd[4] = {0.0, 0.0, 0.0, 0.0};
     for (int base = lo + 16 * warp; base <= hi; base += 64) {
         // each lane prepares one bin of the chunk (lanes 16..31 repeat lanes 0..15)
         const int b = base + (lane & 15);
@@ -413,30 +417,41 @@ __global__ void __launch_bounds__(128) reweight_bf16_kernel(BinData d, const dou
                                                                                  : g == 5 ? vq : 0.f;
             col[q] = Gq > -1e29f ? cv : 0.f;
         }
-        uint32_t ah[4], al[4], bh[2], bl[2];
+        uint32_t ah[4], am[4], al[4], bh[2], bm[2], bl[2];
+        // three-term split of a pair of FP32 values into packed BF16 registers
+        auto split3 = [](float v0, float v1, uint32_t &h, uint32_t &m, uint32_t &l) {
+            const float h0 = bf16_round(v0), h1 = bf16_round(v1);
+            const float m0 = bf16_round(v0 - h0), m1 = bf16_round(v1 - h1);
+            h = pack_bf16x2(h0, h1);
+            m = pack_bf16x2(m0, m1);
+            l = pack_bf16x2((v0 - h0) - m0, (v1 - h1) - m1);
+        };
         // A registers: {row g, bins q0,q1}, {row g+8, q0,q1}, {row g, q2,q3}, {row g+8, q2,q3}
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int row = r & 1, qp = (r >> 1) * 2;
-            const float h0 = bf16_round(x[row][qp]), h1 = bf16_round(x[row][qp + 1]);
-            ah[r] = pack_bf16x2(h0, h1);
-            al[r] = pack_bf16x2(x[row][qp] - h0, x[row][qp + 1] - h1);
+            split3(x[row][qp], x[row][qp + 1], ah[r], am[r], al[r]);
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const float h0 = bf16_round(col[2 * r]), h1 = bf16_round(col[2 * r + 1]);
-            bh[r] = pack_bf16x2(h0, h1);
-            bl[r] = pack_bf16x2(col[2 * r] - h0, col[2 * r + 1] - h1);
-        }
-        mma_bf16_16816(acc, ah, bh);
+        for (int r = 0; r < 2; ++r) split3(col[2 * r], col[2 * r + 1], bh[r], bm[r], bl[r]);
+        // smallest products first
+        mma_bf16_16816(acc, am, bm);
         mma_bf16_16816(acc, ah, bl);
         mma_bf16_16816(acc, al, bh);
+        mma_bf16_16816(acc, ah, bm);
+        mma_bf16_16816(acc, am, bh);
+        mma_bf16_16816(acc, ah, bh);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            accd[i] += (double)acc[i];
+            acc[i] = 0.f;
+        }
     }
     // accumulators: (row g, cols 2t4, 2t4+1), (row g+8, cols 2t4, 2t4+1)
-    s_red[warp][g][2 * t4] = acc[0];
-    s_red[warp][g][2 * t4 + 1] = acc[1];
-    s_red[warp][g + 8][2 * t4] = acc[2];
-    s_red[warp][g + 8][2 * t4 + 1] = acc[3];
+    s_red[warp][g][2 * t4] = accd[0];
+    s_red[warp][g][2 * t4 + 1] = accd[1];
+    s_red[warp][g + 8][2 * t4] = accd[2];
+    s_red[warp][g + 8][2 * t4 + 1] = accd[3];
     __syncthreads();
     if ((int)threadIdx.x < nt) {
         const int t = threadIdx.x;

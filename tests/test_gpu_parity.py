@@ -312,8 +312,8 @@ def test_errors_and_state(muca):
                                               (ISING, 96, 256, 40)])
 def test_reweight_precisions_against_oracle(muca, model, L, p, sweeps):
     """FP64 / FP32 / BF16 tensor-core reweighting against the oracle's FP64 binned form:
-    FP64 within 1e-10, FP32 within 1e-6 (the bar of the reweighting metric), BF16 with
-    its error measured and bounded (hi/lo split products, FP32 accumulation)."""
+    FP64 within 1e-10; FP32 and BF16 (three-term split operands, FP32 accumulation
+    flushed to FP64) within 1e-6, the bar of the reweighting metric."""
     q = 2 if model == ISING else 8
     beta = 0.42 if model == ISING else 1.33
     lnw = random_weights(model, L, 13, beta)
@@ -326,7 +326,7 @@ def test_reweight_precisions_against_oracle(muca, model, L, p, sweeps):
         lnw_g = g.get_lnw()
     ref = reweight.reweight_binned(model, L, q, lnw_g,
                                    *reweight.bin_series(model, L, E_rec, M_rec), betas)
-    bounds = {"fp64": 1e-10, "fp32": 1e-6, "bf16": 2e-3}
+    bounds = {"fp64": 1e-10, "fp32": 1e-6, "bf16": 1e-6}
     for prec, r in res.items():
         for k in ("e", "C", "absm", "chi"):
             rel = np.abs(r[k] - ref[k]) / np.maximum(np.abs(ref[k]), 1e-300)
