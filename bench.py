@@ -265,6 +265,7 @@ def run_gpu(args):
             result["reweight"] = reweight_rates(m, g, torch, stream, betas_h, betas_d)
         g.close()
         result["batched"] = batched_comparison(m, torch)
+        result["other_workloads"] = other_workloads(m, torch, stream)
     else:
         g.close()
     if rank == 0:
@@ -302,6 +303,65 @@ def reweight_rates(m, g, torch, stream, betas_h, betas_d):
         out[name + "_within_1e-6"] = bool(err.max() <= 1e-6)
     out["n_beta"] = n_beta
     out["n_bins"] = g.n_bins
+    return out
+
+
+def other_workloads(m, torch, stream):
+    """Rates of the other configurations on a bounded part of their schedules (each line
+    says which): 8-Potts 32x32 (one 500-sweep weight iteration from ln W = 0, then
+    2000 production sweeps at the fixed canonical weights of beta_0 after 200
+    thermalisation sweeps, reweighted to its 1024 betas) and the large lattices at
+    fixed ln W = -beta_0 E (100 production sweeps, 4096 betas).  Device time by CUDA
+    events on the context's stream; FP32 and BF16 reweighting errors against FP64."""
+    out = {}
+    cases = (("potts8_L32_p4096", 500, 2000), ("ising_L256_p8192", 0, 100), ("potts8_L128_p4096", 0, 100))
+    for name, it_sweeps, prod in cases:
+        w = workloads.WORKLOADS[name]
+        g = m.Muca(w["model"], w["L"], w["q"], w["p"], w["seed"], stream=stream.cuda_stream)
+        V = w["L"] * w["L"]
+        rec = {"sample": "%s%d production sweeps, %d betas"
+               % ("one %d-sweep iteration, " % it_sweeps if it_sweeps else "", prod, w["betas"][2])}
+
+        def timed(fn):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) * 1e-3
+
+        with torch.cuda.stream(stream):
+            if it_sweeps:
+                g.iterate(2)
+                g.update_weights()
+                t = timed(lambda: m.check(m.lib().muca_iterate(g.handle, it_sweeps, None)))
+                rec["iterate_attempts_per_ns"] = w["p"] * V * it_sweeps / t / 1e9
+            beta0 = workloads.ISING_BETA0 if w["model"] == workloads.ISING else workloads.POTTS8_BETA0
+            lnw = workloads.canonical_lnw(w["model"], w["L"], w.get("fixed_beta", beta0))
+            g.set_lnw(lnw - lnw.max())
+            g.thermalize(200 if it_sweeps else 20)
+            g.reset_samples()
+            t = timed(lambda: m.check(m.lib().muca_produce(g.handle, prod, None, None)))
+            rec["produce_attempts_per_ns"] = w["p"] * V * prod / t / 1e9
+            betas_h = workloads.beta_grid(w["betas"])
+            betas_d = torch.tensor(betas_h, dtype=torch.float64, device="cuda")
+            n_beta = len(betas_h)
+            res = {}
+            for prec_name, prec in (("fp64", m.MUCA_FP64), ("fp32", m.MUCA_FP32), ("bf16", m.MUCA_BF16)):
+                o = torch.empty((4, n_beta), dtype=torch.float64, device="cuda")
+                g.reweight(betas_d, prec, out=o)
+                reps = 5
+                t = timed(lambda: [g.reweight(betas_d, prec, out=o) for _ in range(reps)]) / reps
+                rec[prec_name + "_betas_per_s"] = n_beta / t
+                res[prec_name] = o.cpu().numpy()
+            for prec_name in ("fp32", "bf16"):
+                err = np.abs(res[prec_name] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
+                rec[prec_name + "_max_rel_err"] = float(err.max())
+                rec[prec_name + "_within_1e-6"] = bool(err.max() <= 1e-6)
+        g.close()
+        out[name] = rec
     return out
 
 

@@ -607,17 +607,35 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
 
 // ===========================================================================
 // 8-state Potts: warp 0 decides (and fills the histogram / records), warps 1..3
-// produce the Philox blocks (two per site pair; half a block per attempt).
-// A ring slot holds up to 8 words (32 sites) of one row.
+// produce.  A ring slot holds up to 8 words (32 sites) of one row; the ring has three
+// slots and slot s always belongs to producer s, so each hand-off barrier has two
+// parties (the decider and that producer) and the producers run independently of
+// each other.  Per word of 4 sites the producer writes the four clamped
+// acceptance draws, the proposed spins and, byte-parallel, each site's table column
+// (dE + 4) for the previous attempt rejected / accepted, counted over the neighbours
+// whose values are fixed before the decider reaches the site: the old spins below, to
+// the right and to the left, and the left neighbour's proposal.  The decider adds the
+// upper neighbour (the row above is already updated), the right neighbour of a row's
+// last site (site 0, updated at the start of the row) and the left neighbour of a slot
+// that starts mid-row.
 // ===========================================================================
 constexpr int kPottsSlotWords = 8;
-constexpr int kPottsRing = 4;
+constexpr int kPottsRing = 3;  // = number of producers
 
 __device__ __forceinline__ int zero_bytes_ws(uint32_t x)
 {
     const uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
     return __popc(~t & 0x80808080u);
 }
+
+// 0x01 in every byte where x and y are equal, 0x00 elsewhere
+__device__ __forceinline__ uint32_t eq_bytes(uint32_t x, uint32_t y)
+{
+    const uint32_t t = x ^ y;
+    return (~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u) >> 7;
+}
+
+__device__ __forceinline__ uint32_t byte_of(uint32_t x, int k) { return (x >> (8 * k)) & 0xFFu; }
 
 __device__ __forceinline__ void potts_count_move(uint64_t &lo, uint64_t &hi, uint32_t from, uint32_t to)
 {
@@ -646,15 +664,14 @@ __device__ __forceinline__ void potts_count_word(uint32_t word, uint32_t (&cnt)[
 template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
 __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
-    constexpr int NP = 3;
-    constexpr int NT = 128;
-    constexpr int NU = 128;
+    constexpr int NT = 128;         // decider + one producer warp per ring slot
+    constexpr int NU = 64;          // decider + the slot's producer
     __syncthreads();  // smem may still be read by a previous work unit of this block
     const int n_tab = a.n_bins * 9;
     uint32_t *s_tab = smem;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
-    uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][16][32]
+    uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][8 words][2][32]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int c = cblk * 32 + lane;
@@ -669,35 +686,69 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     __syncthreads();
 
     const int L = a.L, RW = a.row_words, V = L * L;
-    const int slots_per_row = (RW + kPottsSlotWords - 1) / kPottsSlotWords;
-    const int total = a.n_sweeps * L * slots_per_row;
+    const int spr = (RW + kPottsSlotWords - 1) / kPottsSlotWords;  // slots per row
+    const int total = a.n_sweeps * L * spr;                          // slots per launch
+    // A producer reads row y+1 (old) and, for the last row, row 0 of the current sweep
+    // (new), so it may run at most L - 1 rows of slots ahead: 3 <= spr * (L - 1) for L >= 4.
+    constexpr int RD = kPottsRing;
+    uint32_t *lp = LSMEM ? s_lat + lane : a.lat + c;
+    const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
+#define LAT(k) lp[(size_t)(k) * ls]
 
     if (warp >= 1) {
         // ---------------- producers ----------------------------------------------
         const int pr = warp - 1;
         uint32_t k1r[10];
         philox_round_keys((uint32_t)c, k1r);
+        const uint32_t cap = active ? 0xFFFFFFFEu : 0xFFFFFFFFu;
+        auto draw = [&](uint32_t x) { return active ? min(x, cap) : cap; };
+        // proposal offset floor(7 w / 2^32) in 0..6, exactly: 7w = 8w - w
+        auto offset7 = [](uint32_t x) { return (x >> 29) - ((x << 3) < x ? 1u : 0u); };
         int it = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
             for (int y = 0; y < L; ++y) {
+                const int kr = y * RW, kd = (y == L - 1 ? 0 : y + 1) * RW;
                 for (int w0 = 0; w0 < RW; w0 += kPottsSlotWords, ++it) {
+                    if (it % RD != pr) continue;  // another producer's slot
                     const int nw = min(kPottsSlotWords, RW - w0);
-                    const int slot = it % kPottsRing;
-                    if (it >= kPottsRing) bar_sync(kBarEmptyU + slot, NU);
-                    uint4 *dst = s_ring + slot * 16 * 32 + lane;
-                    const uint32_t g0 = (uint32_t)(y * L + 4 * w0) >> 1;  // first site pair
-#pragma unroll 6
-                    for (int bi = pr; bi < 2 * nw; bi += NP) {
-                        uint4 b = philox4x32_10_rk(make_uint4(g0 + (uint32_t)bi, ctr1, a.iteration, a.ctr3), a.key0,
-                                                   k1r);
-                        // acceptance draws clamped so that u < A decides; padding chains never accept
-                        b.x = active ? min(b.x, 0xFFFFFFFEu) : 0xFFFFFFFFu;
-                        b.z = active ? min(b.z, 0xFFFFFFFEu) : 0xFFFFFFFFu;
-                        // proposal offsets floor(7 w / 2^32) in 0..6, exactly: 7w = 8w - w
-                        b.y = (b.y >> 29) - ((b.y << 3) < b.y ? 1u : 0u);
-                        b.w = (b.w >> 29) - ((b.w << 3) < b.w ? 1u : 0u);
-                        dst[bi * 32] = b;
+                    const int slot = pr;
+                    if (it >= RD) bar_sync(kBarEmptyU + slot, NU);
+                    {
+                        uint4 *dst = s_ring + slot * 16 * 32 + lane;
+                        // left neighbour of the slot's first site: site L-1 (old) at a row
+                        // start; mid-row it is added by the decider (0xFF matches no spin)
+                        uint32_t lprev = (w0 == 0) ? (LAT(kr + RW - 1) >> 24) : 0xFFu;
+                        uint32_t snprev = 0xFFu;
+                        uint32_t R = LAT(kr + w0);
+#pragma unroll 2
+                        for (int w = w0; w < w0 + nw; ++w) {
+                            const bool lastw = (w == RW - 1);
+                            // right word (old); at the row end the decider adds site 0
+                            const uint32_t Rn = lastw ? 0xFFu : LAT(kr + w + 1);
+                            const uint32_t D = LAT(kd + w);
+                            const uint32_t g = (uint32_t)(y * L + 4 * w) >> 1;
+                            const uint4 b0 = philox4x32_10_rk(make_uint4(g, ctr1, a.iteration, a.ctr3), a.key0, k1r);
+                            const uint4 b1 =
+                                philox4x32_10_rk(make_uint4(g + 1u, ctr1, a.iteration, a.ctr3), a.key0, k1r);
+                            const uint32_t off = offset7(b0.y) | (offset7(b0.w) << 8) | (offset7(b1.y) << 16) |
+                                                 (offset7(b1.w) << 24);
+                            const uint32_t SN = (R + 0x01010101u + off) & 0x07070707u;  // (s + 1 + off) mod 8
+                            const uint32_t Rr = (R >> 8) | (Rn << 24);
+                            const uint32_t Ll = (R << 8) | lprev;
+                            const uint32_t SNl = (SN << 8) | snprev;
+                            const uint32_t base = 0x04040404u + eq_bytes(D, R) + eq_bytes(Rr, R) - eq_bytes(D, SN) -
+                                                  eq_bytes(Rr, SN);
+                            const uint32_t c0 = base + eq_bytes(Ll, R) - eq_bytes(Ll, SN);
+                            uint32_t c1 = base + eq_bytes(SNl, R) - eq_bytes(SNl, SN);
+                            // a row's first site: its left neighbour is not the previous attempt
+                            if (w == 0) c1 = (c1 & 0xFFFFFF00u) | (c0 & 0xFFu);
+                            dst[(2 * (w - w0)) * 32] = make_uint4(draw(b0.x), draw(b0.z), draw(b1.x), draw(b1.z));
+                            dst[(2 * (w - w0) + 1) * 32] = make_uint4(SN, c0, c1, 0u);
+                            lprev = R >> 24;
+                            snprev = SN >> 24;
+                            R = Rn;
+                        }
                     }
                     bar_arrive(kBarFullU + slot, NU);
                 }
@@ -705,13 +756,10 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
         }
     } else {
         // ---------------- decider ------------------------------------------------
-        uint32_t *lp = LSMEM ? s_lat + lane : a.lat + c;
-        const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
-#define LAT(k) lp[(size_t)(k) * ls]
         const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
         const char *tab_g = reinterpret_cast<const char *>(a.ktab) - tab_s;
 #define TABLOAD(o) (TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(tab_g + (o))))
-        int bin = active ? a.E[c] + 2 * V : V;  // bin after the latest attempt
+        const int bin0 = active ? a.E[c] + 2 * V : V;
         uint64_t cnt_lo = 0, cnt_hi = 0;
         if (RECORD && active) {
             uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -721,150 +769,168 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 cnt_hi |= (uint64_t)cnt[k + 4] << (16 * k);
             }
         }
-        // deferred state: P0/P1 = 36 * bin before this attempt if the previous attempt
-        // was rejected / accepted
-        uint32_t P0 = 36u * (uint32_t)bin, P1 = P0;
+        // P0/P1 = table address of the row of the bin before this attempt if the previous
+        // attempt was rejected / accepted (36 bytes per bin)
+        uint32_t P0 = tab_s + 36u * (uint32_t)bin0, P1 = P0;
         bool ap = false;
-        int run_bin = bin;
+        int run_bin = bin0;
         uint32_t run = 0;
-        int it = 0;
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            for (int y = 0; y < L; ++y) {
-                const int kr = y * RW;
-                const int ku = (y == 0 ? L - 1 : y - 1) * RW;
-                const int kd = (y == L - 1 ? 0 : y + 1) * RW;
-                uint32_t R = LAT(kr), U = LAT(ku), D = LAT(kd);
-                uint32_t left0 = LAT(kr + RW - 1) >> 24, left1 = left0;  // site L-1, old
-                uint32_t first_new = 0u;
-                for (int w0 = 0; w0 < RW; w0 += kPottsSlotWords, ++it) {
-                    const int nw = min(kPottsSlotWords, RW - w0);
-                    const int slot = it % kPottsRing;
-                    bar_sync(kBarFullU + slot, NU);
-                    const uint4 *src = s_ring + slot * 16 * 32 + lane;
-                    // per-site constants: offsets of the two table candidates and dE
-                    auto consts = [&](uint32_t Rw_, uint32_t Uw, uint32_t Dw, uint32_t right, uint32_t pw, int k,
-                                      uint32_t l0, uint32_t l1, bool rowstart, uint32_t &s, uint32_t &sn,
-                                      int &dE0, int &dE1) {
-                        s = (Rw_ >> (8 * k)) & 0xFFu;
-                        sn = (s + 1u + pw) & 7u;  // pw: proposal offset from the producer
-                        const uint32_t ud = __byte_perm(Uw, Dw, (uint32_t)(k | ((k + 4) << 4)));
-                        const uint32_t nb3 = __byte_perm(ud, right | 0xFF00u, 0x5410u);
-                        const int base = zero_bytes_ws(nb3 ^ (0x01010101u * s)) - zero_bytes_ws(nb3 ^ (0x01010101u * sn));
-                        dE0 = base + (l0 == s) - (l0 == sn);
-                        dE1 = rowstart ? dE0 : base + (l1 == s) - (l1 == sn);
-                    };
-                    bool loaded = false;   // candidates of the next site already in flight
-                    uint32_t A0 = 0u, A1 = 0u;
-                    uint32_t s_c = 0u, sn_c = 0u;
-                    int dE0_c = 0, dE1_c = 0;
-                    for (int w = w0; w < w0 + nw; ++w) {
-                        const bool lastw = (w == RW - 1);
-                        const bool slot_last = (w == w0 + nw - 1);
-                        uint32_t Rn = 0u, Un = 0u, Dn = 0u;
-                        if (!lastw) {
-                            Rn = LAT(kr + w + 1);
-                            Un = LAT(ku + w + 1);
-                            Dn = LAT(kd + w + 1);
-                        }
-                        const uint4 b0 = src[(2 * (w - w0)) * 32], b1 = src[(2 * (w - w0) + 1) * 32];
-                        uint4 nb0 = b0;
-                        if (!slot_last) nb0 = src[(2 * (w - w0) + 2) * 32];
-                        uint32_t Rw = R;
-                        if (!loaded) {
-                            // first site of the slot: constants and loads now
-                            const uint32_t right = (R >> 8) & 0xFFu;
-                            consts(R, U, D, right, b0.y, 0, left0, left1, w == 0, s_c, sn_c, dE0_c, dE1_c);
-                            A0 = TABLOAD(P0 + tab_s + 4u * (uint32_t)(dE0_c + 4));
-                            A1 = TABLOAD(P1 + tab_s + 4u * (uint32_t)(dE1_c + 4));
-                        }
+        // bin of a table row address: (P - tab_s) / 36 = ((P - tab_s) / 4) * 9^-1 mod 2^32
+        auto bin_of = [&](uint32_t P) { return (int)(((P - tab_s) >> 2) * 0x38E38E39u); };
+
+        // word context: old spins, proposals, draws and the two column words x 4
+        struct PW {
+            uint32_t R, SN, C0, C1;
+            uint4 u;
+        };
+        // columns of a word: the producer's counts plus the upper neighbour; a slot that
+        // starts mid-row also gets its first site's left neighbour (old spin, proposal)
+        auto columns = [&](PW &x, const uint4 &r1, uint32_t U, bool slot_mid, uint32_t lold, uint32_t lsn) {
+            x.SN = r1.x;
+            const uint32_t up = eq_bytes(U, x.R), un = eq_bytes(U, x.SN);
+            uint32_t c0 = r1.y + up - un, c1 = r1.z + up - un;
+            if (slot_mid) {
+                const uint32_t s0 = x.R & 0xFFu, sn0 = x.SN & 0xFFu;
+                c0 = c0 + (lold == s0 ? 1u : 0u) - (lold == sn0 ? 1u : 0u);
+                c1 = c1 + (lsn == s0 ? 1u : 0u) - (lsn == sn0 ? 1u : 0u);
+            }
+            x.C0 = c0 << 2;
+            x.C1 = c1 << 2;
+        };
+
+        const int total_words = a.n_sweeps * L * RW;
+        // the first word
+        bar_sync(kBarFullU + 0, NU);
+        PW cur;
+        {
+            cur.R = LAT(0);
+            cur.u = s_ring[lane];
+            columns(cur, s_ring[32 + lane], LAT((L - 1) * RW), false, 0u, 0u);
+        }
+        uint32_t K0 = cur.C0 & 0xFFu, K1 = cur.C1 & 0xFFu;
+        uint32_t D0 = 9u * K0 - 144u, D1 = 9u * K1 - 144u;
+        uint32_t A0 = TABLOAD(P0 + K0), A1 = TABLOAD(P1 + K1);
+        int y = 0, w = 0, sw = 0, it = 0;
+        uint32_t first_new = 0u;
+        for (int q = 0; q < total_words; ++q) {
+            const bool lastw = (w == RW - 1);
+            const bool has_next = q + 1 < total_words;
+            int y1 = y, w1 = w + 1;
+            if (w1 == RW) {
+                w1 = 0;
+                y1 = (y + 1 == L) ? 0 : y + 1;
+            }
+            const bool new_slot = (w1 % kPottsSlotWords) == 0;  // the next word opens a slot
+            const int it1 = it + (new_slot ? 1 : 0);
+            // next word: its slot, records, old spins and row above (new)
+            PW nx;
+            nx.R = 0u;
+            nx.SN = nx.C0 = nx.C1 = 0u;
+            nx.u = make_uint4(0u, 0u, 0u, 0u);
+            uint4 nr1 = nx.u;
+            uint32_t nU = 0u;
+            if (has_next) {
+                if (new_slot) bar_sync(kBarFullU + it1 % RD, NU);
+                const uint4 *src1 = s_ring + (it1 % RD) * 16 * 32 + (2 * (w1 % kPottsSlotWords)) * 32 + lane;
+                nx.u = src1[0];
+                nr1 = src1[32];
+                nx.R = LAT(y1 * RW + w1);
+                nU = LAT((y1 == 0 ? L - 1 : y1 - 1) * RW + w1);
+            }
+            uint32_t Fm = 0u;  // bytes of accepted sites
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint32_t u = k == 0 ? b0.x : k == 1 ? b0.z : k == 2 ? b1.x : b1.z;
-                            // 1. constants and candidate loads of the next site
-                            uint32_t s_n = 0u, sn_n = 0u;
-                            int dE0_n = 0, dE1_n = 0;
-                            uint32_t A0n = 0u, A1n = 0u;
-                            const bool has_next = (k < 3) || !slot_last;
-                            uint32_t nP0 = ap ? P1 : P0;
-                            uint32_t nP1 = ap ? P1 + (uint32_t)(36 * dE1_c) : P0 + (uint32_t)(36 * dE0_c);
-                            if (has_next) {
-                                if (k < 3) {
-                                    const uint32_t pw = k == 0 ? b0.w : k == 1 ? b1.y : b1.w;
-                                    const uint32_t right = k < 2 ? (R >> (8 * (k + 2))) & 0xFFu
-                                                                 : (lastw ? first_new : (Rn & 0xFFu));
-                                    consts(R, U, D, right, pw, k + 1, s_c, sn_c, false, s_n, sn_n, dE0_n, dE1_n);
-                                } else {
-                                    const uint32_t right = (Rn >> 8) & 0xFFu;
-                                    consts(Rn, Un, Dn, right, nb0.y, 0, s_c, sn_c, false, s_n, sn_n, dE0_n, dE1_n);
-                                }
-                                const uint32_t o0 = (ap ? P1 : P0) + tab_s + 4u * (uint32_t)(dE0_n + 4);
-                                const uint32_t o1 = nP1 + tab_s + 4u * (uint32_t)(dE1_n + 4);
-                                A0n = TABLOAD(o0);
-                                A1n = TABLOAD(o1);
-                            }
-                            // 2. decision of this site
-                            const uint32_t A = ap ? A1 : A0;
-                            const bool acc = u < A;
-                            const int dE = ap ? dE1_c : dE0_c;
-                            bin += acc ? dE : 0;
-                            const uint32_t mask = 0xFFu << (8 * k);
-                            Rw = acc ? ((Rw & ~mask) | (sn_c << (8 * k))) : Rw;
-                            if (RECORD && acc) potts_count_move(cnt_lo, cnt_hi, s_c, sn_c);
-                            if (k == 0 && w == 0) first_new = acc ? sn_c : s_c;
-                            if (HIST) {
-                                if (HSMEM) {
-                                    if (active) red_shared(s_hist + bin, 1u);
-                                } else {
-                                    if (bin != run_bin) {
-                                        if (active)
-                                            atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]),
-                                                      (unsigned long long)run);
-                                        run_bin = bin;
-                                        run = 0;
-                                    }
-                                    ++run;
-                                }
-                            }
-                            // 3. state of the next site
-                            P0 = nP0;
-                            P1 = nP1;
-                            A0 = A0n;
-                            A1 = A1n;
-                            s_c = s_n;
-                            sn_c = sn_n;
-                            dE0_c = dE0_n;
-                            dE1_c = dE1_n;
-                            ap = acc;
-                        }
-                        loaded = !slot_last;
-                        if (slot_last && !lastw) {
-                            // next slot starts mid-row: its first site's left neighbour
-                            left0 = (R >> 24) & 0xFFu;
-                            left1 = (Rw >> 24) & 0xFFu;
-                            left1 = ap ? left1 : left0;
-                            left0 = left1;
-                        }
-                        LAT(kr + w) = Rw;
-                        R = Rn;
-                        U = Un;
-                        D = Dn;
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t u = k == 0 ? cur.u.x : k == 1 ? cur.u.y : k == 2 ? cur.u.z : cur.u.w;
+                if (k == 1 && RW > 1 && has_next)
+                    columns(nx, nr1, nU, new_slot && w1 != 0, cur.R >> 24, cur.SN >> 24);
+                if (k == 3 && RW == 1 && has_next) {
+                    // one word per row: the row above of the next word is this word, whose
+                    // sites 0..2 are final here (site 0 is all the next site needs)
+                    nU = (cur.R & ~Fm) | (cur.SN & Fm);
+                    columns(nx, nr1, nU, false, 0u, 0u);
+                }
+                // 1. candidates of the next site
+                uint32_t Kn0 = 0u, Kn1 = 0u;
+                if (k < 3) {
+                    Kn0 = byte_of(cur.C0, k + 1);
+                    Kn1 = byte_of(cur.C1, k + 1);
+                    if (k == 2 && lastw) {
+                        // row end: the right neighbour of site 3 is site 0 of the row, new
+                        const uint32_t s3 = cur.R >> 24, sn3 = cur.SN >> 24;
+                        const uint32_t dK = (first_new == s3 ? 4u : 0u) - (first_new == sn3 ? 4u : 0u);
+                        Kn0 += dK;
+                        Kn1 += dK;
                     }
-                    if (it < total - kPottsRing) bar_arrive(kBarEmptyU + slot, NU);
+                } else {
+                    Kn0 = nx.C0 & 0xFFu;
+                    Kn1 = nx.C1 & 0xFFu;
                 }
-            }
-            if (RECORD && active) {
-                const int E = bin - 2 * V;
-                const int M = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
-                if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
-                if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
-                if (a.samples) {
-                    const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
-                    unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
-                    atomicAdd(&sp[bin], 1ull);
-                    atomicAdd(&sp[a.n_bins + bin], am);
-                    atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+                const uint32_t Dn0 = 9u * Kn0 - 144u, Dn1 = 9u * Kn1 - 144u;
+                const uint32_t Pb = ap ? P1 : P0;
+                const uint32_t PbD = ap ? P1 + D1 : P0 + D0;
+                uint32_t A0n = 0u, A1n = 0u;
+                if (k < 3 || has_next) {
+                    A0n = TABLOAD(Pb + Kn0);
+                    A1n = TABLOAD(PbD + Kn1);
                 }
+                // 2. decision of this site
+                const uint32_t A = ap ? A1 : A0;
+                const bool acc = u < A;
+                Fm |= acc ? (0xFFu << (8 * k)) : 0u;
+                if (k == 0 && w == 0) first_new = acc ? (cur.SN & 0xFFu) : (cur.R & 0xFFu);
+                const uint32_t Pa = acc ? PbD : Pb;  // bin row after this attempt
+                if (RECORD && acc) potts_count_move(cnt_lo, cnt_hi, byte_of(cur.R, k), byte_of(cur.SN, k));
+                if (HIST) {
+                    const int bin = bin_of(Pa);
+                    if (HSMEM) {
+                        if (active) red_shared(s_hist + bin, 1u);
+                    } else {
+                        if (bin != run_bin) {
+                            if (active)
+                                atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]),
+                                          (unsigned long long)run);
+                            run_bin = bin;
+                            run = 0;
+                        }
+                        ++run;
+                    }
+                }
+                // 3. state of the next site
+                P0 = Pb;
+                P1 = PbD;
+                D0 = Dn0;
+                D1 = Dn1;
+                A0 = A0n;
+                A1 = A1n;
+                ap = acc;
             }
+            LAT(y * RW + w) = (cur.R & ~Fm) | (cur.SN & Fm);
+            // one word per row: now that this word is final, the next word's columns
+            // (its sites 1..3) get their upper neighbours
+            if (RW == 1 && has_next) columns(nx, nr1, (cur.R & ~Fm) | (cur.SN & Fm), false, 0u, 0u);
+            // the slot's records are all read: release it
+            if (new_slot && it < total - RD) bar_arrive(kBarEmptyU + it % RD, NU);
+            if (lastw && y == L - 1) {
+                if (RECORD && active) {
+                    const int bin = bin_of(ap ? P1 : P0);
+                    const int E = bin - 2 * V;
+                    const int M = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
+                    if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
+                    if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
+                    if (a.samples) {
+                        const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
+                        unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
+                        atomicAdd(&sp[bin], 1ull);
+                        atomicAdd(&sp[a.n_bins + bin], am);
+                        atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+                    }
+                }
+                ++sw;
+            }
+            cur = nx;
+            y = y1;
+            w = w1;
+            it = it1;
         }
         if (active) {
             if (HIST && !HSMEM && run)
@@ -878,7 +944,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                     cnt_hi |= (uint64_t)cnt[k + 4] << (16 * k);
                 }
             }
-            a.E[c] = bin - 2 * V;
+            a.E[c] = bin_of(ap ? P1 : P0) - 2 * V;
             a.M[c] = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
             a.cnt[c] = cnt_lo;
             a.cnt[a.p_pad + c] = cnt_hi;
@@ -886,8 +952,8 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
 #undef TABLOAD
         if (LSMEM)
             for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
-#undef LAT
     }
+#undef LAT
     __syncthreads();
     if (HIST && HSMEM) {
         for (int i = tid; i < a.n_bins; i += NT) {
