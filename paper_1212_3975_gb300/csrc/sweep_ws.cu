@@ -12,11 +12,12 @@ __global__ void __launch_bounds__(128) ising_ws_kernel(SweepArgs a)
     ising_ws_body<HIST, RECORD, TSMEM, HSMEM, LSMEM>(a, blockIdx.x, smem);
 }
 
+// iteration and production launches: five warps (decider, 3 producers, bookkeeper)
 template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
-__global__ void __launch_bounds__(128) potts_ws_kernel(SweepArgs a)
+__global__ void __launch_bounds__(160) potts_ws_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    potts_ws_body<HIST, RECORD, TSMEM, HSMEM, LSMEM>(a, blockIdx.x, smem);
+    potts_ws_body<HIST, RECORD, TSMEM, HSMEM, LSMEM, true>(a, blockIdx.x, smem);
 }
 
 template <int MODEL, bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
@@ -28,7 +29,7 @@ cudaError_t launch_ws(const SweepArgs &a, int blocks, size_t smem, cudaStream_t 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<blocks, 128, smem, st>>>(a);
+    kern<<<blocks, (MODEL == MUCA_POTTS && (HIST || RECORD)) ? 160 : 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -54,7 +55,7 @@ cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size
 size_t ws_extra_smem(int model)
 {
     return model == MUCA_ISING ? (size_t)kRingU * 8 * 32 * sizeof(uint4) + (size_t)kRingS * 32 * sizeof(Snap)
-                               : potts_ws_extra_smem();
+                               : potts_ws_extra_smem(true);
 }
 
 cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,

@@ -661,19 +661,26 @@ __device__ __forceinline__ void potts_count_word(uint32_t word, uint32_t (&cnt)[
     for (int k = 0; k < 8; ++k) cnt[k] += zero_bytes_ws(word ^ (0x01010101u * (uint32_t)k));
 }
 
-template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+// PBOOK: a fifth warp, the bookkeeper, takes the histogram, the state counts and the
+// records from per-word snapshots (iteration and production launches of the
+// standalone kernel); the decider then runs on warp 1, alone on its SM sub-partition,
+// and the bookkeeper shares one with producer warp 0.
+template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM, bool PBOOK = false>
 __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
-    constexpr int NT = 128;         // decider + one producer warp per ring slot
-    constexpr int NU = 64;          // decider + the slot's producer
+    constexpr bool BOOKW = PBOOK && (HIST || RECORD);
+    constexpr int NT = BOOKW ? 160 : 128;  // decider + one producer warp per ring slot (+ bookkeeper)
+    constexpr int NU = 64;                 // decider + the slot's producer
     __syncthreads();  // smem may still be read by a previous work unit of this block
     const int n_tab = a.n_bins * 9;
     uint32_t *s_tab = smem;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][8 words][2][32]
+    uint4 *s_psnap = s_ring + kPottsRing * 16 * 32;                                      // [kRingS][2][32]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int vw = BOOKW ? (warp == 0 ? 1 : warp == 1 ? 0 : warp) : warp;  // role: 0 decider, 1..3 producers, 4 bookkeeper
     const int c = cblk * 32 + lane;
     const bool active = c < a.p;
 
@@ -681,8 +688,20 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
         for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
     if (HIST && HSMEM)
         for (int i = tid; i < a.n_bins; i += NT) s_hist[i] = 0u;
-    if (LSMEM && warp == 0)
+    if (LSMEM && vw == 0)
         for (int k = 0; k < a.lat_words; ++k) s_lat[k * 32 + lane] = a.lat[(size_t)k * a.p_pad + c];
+    // bookkeeper of a production launch: state counts of the starting lattice, read
+    // before the decider changes it
+    uint64_t bk_lo = 0, bk_hi = 0;
+    const int bk_bin0 = active ? a.E[c] + 2 * a.L * a.L : a.L * a.L;  // bin at the start
+    if (BOOKW && RECORD && vw == 4 && active) {
+        uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < a.lat_words; ++k) potts_count_word(a.lat[(size_t)k * a.p_pad + c], cnt);
+        for (int k = 0; k < 4; ++k) {
+            bk_lo |= (uint64_t)cnt[k] << (16 * k);
+            bk_hi |= (uint64_t)cnt[k + 4] << (16 * k);
+        }
+    }
     __syncthreads();
 
     const int L = a.L, RW = a.row_words, V = L * L;
@@ -695,9 +714,9 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
 #define LAT(k) lp[(size_t)(k) * ls]
 
-    if (warp >= 1) {
+    if (vw >= 1 && vw <= kPottsRing) {
         // ---------------- producers ----------------------------------------------
-        const int pr = warp - 1;
+        const int pr = vw - 1;
         uint32_t k1r[10];
         philox_round_keys((uint32_t)c, k1r);
         const uint32_t cap = active ? 0xFFFFFFFEu : 0xFFFFFFFFu;
@@ -754,14 +773,14 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 }
             }
         }
-    } else {
+    } else if (vw == 0) {
         // ---------------- decider ------------------------------------------------
         const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
         const char *tab_g = reinterpret_cast<const char *>(a.ktab) - tab_s;
 #define TABLOAD(o) (TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(tab_g + (o))))
         const int bin0 = active ? a.E[c] + 2 * V : V;
         uint64_t cnt_lo = 0, cnt_hi = 0;
-        if (RECORD && active) {
+        if (RECORD && !BOOKW && active) {
             uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int k = 0; k < a.lat_words; ++k) potts_count_word(LAT(k), cnt);
             for (int k = 0; k < 4; ++k) {
@@ -838,6 +857,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 nU = LAT((y1 == 0 ? L - 1 : y1 - 1) * RW + w1);
             }
             uint32_t Fm = 0u;  // bytes of accepted sites
+            uint32_t Pw[4];    // bin rows after each attempt of the word (bookkeeper)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t u = k == 0 ? cur.u.x : k == 1 ? cur.u.y : k == 2 ? cur.u.z : cur.u.w;
@@ -879,8 +899,9 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 Fm |= acc ? (0xFFu << (8 * k)) : 0u;
                 if (k == 0 && w == 0) first_new = acc ? (cur.SN & 0xFFu) : (cur.R & 0xFFu);
                 const uint32_t Pa = acc ? PbD : Pb;  // bin row after this attempt
-                if (RECORD && acc) potts_count_move(cnt_lo, cnt_hi, byte_of(cur.R, k), byte_of(cur.SN, k));
-                if (HIST) {
+                Pw[k] = Pa;
+                if (RECORD && !BOOKW && acc) potts_count_move(cnt_lo, cnt_hi, byte_of(cur.R, k), byte_of(cur.SN, k));
+                if (HIST && !BOOKW) {
                     const int bin = bin_of(Pa);
                     if (HSMEM) {
                         if (active) red_shared(s_hist + bin, 1u);
@@ -910,8 +931,16 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             if (RW == 1 && has_next) columns(nx, nr1, (cur.R & ~Fm) | (cur.SN & Fm), false, 0u, 0u);
             // the slot's records are all read: release it
             if (new_slot && it < total - RD) bar_arrive(kBarEmptyU + it % RD, NU);
+            if (BOOKW) {
+                const int ss = q % kRingS;
+                if (q >= kRingS) bar_sync(kBarEmptyS + ss, 64);
+                uint4 *sn = s_psnap + ss * 2 * 32 + lane;
+                if (HIST) sn[0] = make_uint4(Pw[0], Pw[1], Pw[2], Pw[3]);
+                if (RECORD) sn[32] = make_uint4(Pw[3], cur.R, cur.SN, Fm);
+                bar_arrive(kBarFullS + ss, 64);
+            }
             if (lastw && y == L - 1) {
-                if (RECORD && active) {
+                if (RECORD && !BOOKW && active) {
                     const int bin = bin_of(ap ? P1 : P0);
                     const int E = bin - 2 * V;
                     const int M = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
@@ -933,7 +962,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             it = it1;
         }
         if (active) {
-            if (HIST && !HSMEM && run)
+            if (HIST && !BOOKW && !HSMEM && run)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
             if (!RECORD) {
                 uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -945,13 +974,80 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 }
             }
             a.E[c] = bin_of(ap ? P1 : P0) - 2 * V;
-            a.M[c] = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
-            a.cnt[c] = cnt_lo;
-            a.cnt[a.p_pad + c] = cnt_hi;
+            if (!(RECORD && BOOKW)) {
+                a.M[c] = 8 * potts_count_max(cnt_lo, cnt_hi) - V;
+                a.cnt[c] = cnt_lo;
+                a.cnt[a.p_pad + c] = cnt_hi;
+            }
         }
 #undef TABLOAD
         if (LSMEM)
             for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
+    } else if (BOOKW && vw == 4) {
+        // ---------------- bookkeeper: histogram, state counts, records -----------
+        const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
+        auto bin_of = [&](uint32_t P) { return (int)(((P - tab_s) >> 2) * 0x38E38E39u); };
+        int run_bin = bk_bin0;
+        uint32_t run = 0;
+        const int total_words = a.n_sweeps * L * RW;
+        const int words_per_sweep = L * RW;
+        for (int q = 0; q < total_words; ++q) {
+            const int ss = q % kRingS;
+            bar_sync(kBarFullS + ss, 64);
+            const uint4 *sn = s_psnap + ss * 2 * 32 + lane;
+            uint4 pb = make_uint4(0u, 0u, 0u, 0u), rs = pb;
+            if (HIST) pb = sn[0];
+            if (RECORD) rs = sn[32];
+            if (q < total_words - kRingS) bar_arrive(kBarEmptyS + ss, 64);
+            if (HIST) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int bin = bin_of(k == 0 ? pb.x : k == 1 ? pb.y : k == 2 ? pb.z : pb.w);
+                    if (HSMEM) {
+                        if (active) red_shared(s_hist + bin, 1u);
+                    } else {
+                        if (bin != run_bin) {
+                            if (active)
+                                atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]),
+                                          (unsigned long long)run);
+                            run_bin = bin;
+                            run = 0;
+                        }
+                        ++run;
+                    }
+                }
+            }
+            if (RECORD) {
+                // rs = (bin row after the word's last attempt, old spins, proposals, accepted bytes)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if ((rs.w >> (8 * k)) & 1u) potts_count_move(bk_lo, bk_hi, byte_of(rs.y, k), byte_of(rs.z, k));
+                if ((q + 1) % words_per_sweep == 0 && active) {
+                    const int sw = q / words_per_sweep;
+                    const int bin = bin_of(rs.x);
+                    const int E = bin - 2 * V;
+                    const int M = 8 * potts_count_max(bk_lo, bk_hi) - V;
+                    if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
+                    if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
+                    if (a.samples) {
+                        const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
+                        unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
+                        atomicAdd(&sp[bin], 1ull);
+                        atomicAdd(&sp[a.n_bins + bin], am);
+                        atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+                    }
+                }
+            }
+        }
+        if (active) {
+            if (HIST && !HSMEM && run)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
+            if (RECORD) {
+                a.M[c] = 8 * potts_count_max(bk_lo, bk_hi) - V;
+                a.cnt[c] = bk_lo;
+                a.cnt[a.p_pad + c] = bk_hi;
+            }
+        }
     }
 #undef LAT
     __syncthreads();
@@ -963,6 +1059,11 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     }
 }
 
-__host__ __device__ constexpr size_t potts_ws_extra_smem() { return (size_t)kPottsRing * 16 * 32 * sizeof(uint4); }
+// shared memory of the Potts body beyond the staging: the draw/column ring and, with
+// the bookkeeper, its snapshot ring
+__host__ __device__ constexpr size_t potts_ws_extra_smem(bool book = false)
+{
+    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) + (book ? (size_t)kRingS * 2 * 32 * sizeof(uint4) : 0);
+}
 }  // namespace ws
 }  // namespace muca
