@@ -635,7 +635,7 @@ __device__ __forceinline__ uint32_t eq_bytes(uint32_t x, uint32_t y)
     return (~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u) >> 7;
 }
 
-__device__ __forceinline__ uint32_t byte_of(uint32_t x, int k) { return (x >> (8 * k)) & 0xFFu; }
+__device__ __forceinline__ uint32_t byte_of(uint32_t x, int k) { return __byte_perm(x, 0u, 0x4440u | (uint32_t)k); }
 
 __device__ __forceinline__ void potts_count_move(uint64_t &lo, uint64_t &hi, uint32_t from, uint32_t to)
 {
@@ -710,9 +710,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     // A producer reads row y+1 (old) and, for the last row, row 0 of the current sweep
     // (new), so it may run at most L - 1 rows of slots ahead: 3 <= spr * (L - 1) for L >= 4.
     constexpr int RD = kPottsRing;
-    uint32_t *lp = LSMEM ? s_lat + lane : a.lat + c;
-    const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
-#define LAT(k) lp[(size_t)(k) * ls]
+#define LAT(k) (*(LSMEM ? &s_lat[(k) * 32 + lane] : &a.lat[(size_t)(k) * a.p_pad + c]))
 
     if (vw >= 1 && vw <= kPottsRing) {
         // ---------------- producers ----------------------------------------------
@@ -763,7 +761,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                             // a row's first site: its left neighbour is not the previous attempt
                             if (w == 0) c1 = (c1 & 0xFFFFFF00u) | (c0 & 0xFFu);
                             dst[(2 * (w - w0)) * 32] = make_uint4(draw(b0.x), draw(b0.z), draw(b1.x), draw(b1.z));
-                            dst[(2 * (w - w0) + 1) * 32] = make_uint4(SN, c0, c1, 0u);
+                            dst[(2 * (w - w0) + 1) * 32] = make_uint4(SN, c0, c1, R);  // R: old spins
                             lprev = R >> 24;
                             snprev = SN >> 24;
                             R = Rn;
@@ -853,7 +851,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 const uint4 *src1 = s_ring + (it1 % RD) * 16 * 32 + (2 * (w1 % kPottsSlotWords)) * 32 + lane;
                 nx.u = src1[0];
                 nr1 = src1[32];
-                nx.R = LAT(y1 * RW + w1);
+                nx.R = nr1.w;
                 nU = LAT((y1 == 0 ? L - 1 : y1 - 1) * RW + w1);
             }
             uint32_t Fm = 0u;  // bytes of accepted sites
