@@ -678,6 +678,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][8 words][2][32]
     uint4 *s_psnap = s_ring + kPottsRing * 16 * 32;                                      // [kRingS][2][32]
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_psnap + kRingS * 2 * 32);          // [8][32] state counts
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vw = BOOKW ? (warp == 0 ? 1 : warp == 1 ? 0 : warp) : warp;  // role: 0 decider, 1..3 producers, 4 bookkeeper
@@ -691,16 +692,13 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     if (LSMEM && vw == 0)
         for (int k = 0; k < a.lat_words; ++k) s_lat[k * 32 + lane] = a.lat[(size_t)k * a.p_pad + c];
     // bookkeeper of a production launch: state counts of the starting lattice, read
-    // before the decider changes it
-    uint64_t bk_lo = 0, bk_hi = 0;
+    // before the decider changes it, one shared-memory counter per state and lane
     const int bk_bin0 = active ? a.E[c] + 2 * a.L * a.L : a.L * a.L;  // bin at the start
-    if (BOOKW && RECORD && vw == 4 && active) {
+    if (BOOKW && RECORD && vw == 4) {
         uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int k = 0; k < a.lat_words; ++k) potts_count_word(a.lat[(size_t)k * a.p_pad + c], cnt);
-        for (int k = 0; k < 4; ++k) {
-            bk_lo |= (uint64_t)cnt[k] << (16 * k);
-            bk_hi |= (uint64_t)cnt[k + 4] << (16 * k);
-        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s_cnt[k * 32 + lane] = cnt[k];
     }
     __syncthreads();
 
@@ -1017,14 +1015,21 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             }
             if (RECORD) {
                 // rs = (bin row after the word's last attempt, old spins, proposals, accepted bytes)
+                // accepted sites move one count from the old state to the new one
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if ((rs.w >> (8 * k)) & 1u) potts_count_move(bk_lo, bk_hi, byte_of(rs.y, k), byte_of(rs.z, k));
+                    if ((rs.w >> (8 * k)) & 1u) {
+                        red_shared(s_cnt + byte_of(rs.y, k) * 32 + lane, 0xFFFFFFFFu);
+                        red_shared(s_cnt + byte_of(rs.z, k) * 32 + lane, 1u);
+                    }
                 if ((q + 1) % words_per_sweep == 0 && active) {
                     const int sw = q / words_per_sweep;
                     const int bin = bin_of(rs.x);
                     const int E = bin - 2 * V;
-                    const int M = 8 * potts_count_max(bk_lo, bk_hi) - V;
+                    uint32_t mx = 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) mx = max(mx, s_cnt[k * 32 + lane]);
+                    const int M = 8 * (int)mx - V;
                     if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
                     if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
                     if (a.samples) {
@@ -1041,9 +1046,18 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             if (HIST && !HSMEM && run)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
             if (RECORD) {
-                a.M[c] = 8 * potts_count_max(bk_lo, bk_hi) - V;
-                a.cnt[c] = bk_lo;
-                a.cnt[a.p_pad + c] = bk_hi;
+                uint64_t lo = 0, hi = 0;
+                uint32_t mx = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t c0 = s_cnt[k * 32 + lane], c1 = s_cnt[(k + 4) * 32 + lane];
+                    lo |= (uint64_t)c0 << (16 * k);
+                    hi |= (uint64_t)c1 << (16 * k);
+                    mx = max(mx, max(c0, c1));
+                }
+                a.M[c] = 8 * (int)mx - V;
+                a.cnt[c] = lo;
+                a.cnt[a.p_pad + c] = hi;
             }
         }
     }
@@ -1061,7 +1075,8 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
 // the bookkeeper, its snapshot ring
 __host__ __device__ constexpr size_t potts_ws_extra_smem(bool book = false)
 {
-    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) + (book ? (size_t)kRingS * 2 * 32 * sizeof(uint4) : 0);
+    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) +
+           (book ? (size_t)kRingS * 2 * 32 * sizeof(uint4) + 8 * 32 * sizeof(uint32_t) : 0);
 }
 }  // namespace ws
 }  // namespace muca
