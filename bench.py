@@ -15,6 +15,7 @@ collective on the data path.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -266,6 +267,7 @@ def run_gpu(args):
         g.close()
         result["batched"] = batched_comparison(m, torch)
         result["other_workloads"] = other_workloads(m, torch, stream)
+        result["statistical_study"] = statistical_study()
     else:
         g.close()
     if rank == 0:
@@ -363,6 +365,28 @@ def other_workloads(m, torch, stream):
         g.close()
         out[name] = rec
     return out
+
+
+def statistical_study():
+    """The performance study of Sec. 4, bounded: 8x8 Ising, p = 1..32 chains, 10 seeds,
+    M on a geometric grid around Eq. 7's M_opt(8, p), runs capped at 400 iterations.
+    M_opt(p) is the minimum of N_iter M p; S*_p comes from the same minima."""
+    from paper_1212_3975_gb300 import study
+    ps = [1, 2, 4, 8, 16, 32]
+    factors = [0.5, 0.7, 1.0, 1.4, 2.0, 2.8, 4.0]
+    t0 = time.perf_counter()
+    scan = study.m_scan(study.ISING, 8, ps, factors, 10, 400)
+    m_opt, per_chain, S = study.speedup_from_scan(scan)
+    m1 = study.fit_m1(ps, [m_opt[p] for p in ps])
+    fin = lambda x: None if not math.isfinite(x) else round(float(x), 3)  # noqa: E731
+    return {
+        "workload": "8x8 Ising, p in 1..32, 10 seeds per (p, M), M grid x{0.5..4} around Eq. 7, <= 400 iterations",
+        "M_opt": {str(p): fin(m_opt[p]) for p in ps},
+        "M1_fit": round(m1, 1), "M1_eq7": round(study.eq7_m_opt(study.ISING, 8, 1), 1),
+        "sweeps_per_chain_to_convergence": {str(p): fin(per_chain[p]) for p in ps},
+        "S_star": {str(p): fin(S[p]) for p in ps},
+        "seconds": round(time.perf_counter() - t0, 2),
+    }
 
 
 def batched_comparison(m, torch):

@@ -134,6 +134,16 @@ int muca_iterate(muca_ctx *ctx, int n_sweeps, uint64_t *H_out);
  * Errors: MUCA_ERR_STATE (no histogram since the last update), MUCA_ERR_CUDA. */
 int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out);
 
+/* Weight iterations until convergence (Sec. 3; the study of Sec. 4 counts them):
+ * muca_iterate(n_sweeps) + muca_update_weights, repeated until the merged histogram
+ * of an iteration is covered and flat, or max_iterations were run.  The update of
+ * the converged iteration is applied, so the context holds the weights that follow
+ * it.  *n_iter_out (host, may be NULL) = the number of iterations run when the last
+ * one converged (the paper's N_iter), -1 if none did; *last (host, may be NULL) = the
+ * statistics of the last iteration.  Synchronises once per iteration.
+ * Errors: MUCA_ERR_ARG (n_sweeps < 1 or max_iterations < 1), MUCA_ERR_CUDA. */
+int muca_converge(muca_ctx *ctx, int n_sweeps, int max_iterations, int *n_iter_out, muca_iter_stats *last);
+
 /* Thermalise every chain with the current weights for n_sweeps sweeps (Sec. 3:
  * "thermalized again" before production); nothing is recorded. */
 int muca_thermalize(muca_ctx *ctx, int n_sweeps);
@@ -234,6 +244,15 @@ int muca_batch_destroy(muca_batch *b);
  * graph (built once per (n_iterations, n_sweeps) and cached); returns when the work
  * is queued.  Errors: MUCA_ERR_ARG, MUCA_ERR_CUDA. */
 int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_graph);
+
+/* Weight iterations of every lattice until each converges (as muca_converge on each
+ * context, and bit-identical to it): a lattice whose merged histogram is covered and
+ * flat freezes in that iteration -- no further sweeps, updates or counter advances --
+ * while the others go on, up to max_iterations.  n_iter_out[n_jobs] (host, may be
+ * NULL) receives each lattice's N_iter, -1 for one that did not converge.  Afterwards
+ * every lattice runs again in later calls.  Synchronises every few iterations.
+ * Errors: MUCA_ERR_ARG, MUCA_ERR_CUDA. */
+int muca_batch_converge(muca_batch *b, int n_sweeps, int max_iterations, int *n_iter_out);
 
 /* The context of job j (owned by the batch; use it for state access). */
 muca_ctx *muca_batch_job(muca_batch *b, int j);

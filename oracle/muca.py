@@ -106,6 +106,19 @@ class MucaOracle:
         self.thr = weights.thresholds(self.model, self.L, self.lnw, self.acc)
         return stats
 
+    def converge(self, n_sweeps, max_iterations):
+        """Weight iterations until convergence (Sec. 3): sweeps of one iteration, then the
+        update; stop after the first iteration whose histogram (before its update) is
+        covered and flat.  Returns (N_iter, its statistics); N_iter = -1 if no
+        iteration up to max_iterations converged."""
+        stats = None
+        for it in range(1, max_iterations + 1):
+            self.iterate(n_sweeps)
+            stats = self.update_weights()
+            if stats["flat"]:
+                return it, stats
+        return -1, stats
+
     def set_lnw(self, lnw):
         self.lnw = np.asarray(lnw, dtype=np.float64).copy()
         self.thr = weights.thresholds(self.model, self.L, self.lnw, self.acc)

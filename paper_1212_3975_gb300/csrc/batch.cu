@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const BatchJob *jobs, 
         if (u >= n_units) break;
         const BatchUnit un = units[u];
         const BatchJob &j = jobs[un.job];
+        if (!*j.active) continue;  // converged: frozen
         const SweepArgs a = batch_args(j, n_sweeps, sweep0);
         if (j.model == MUCA_ISING)
             run_unit<MUCA_ISING>(a, j.flags, un.cblk, smem);
@@ -105,8 +106,9 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const BatchJob *jobs, 
 __global__ void batch_prepare_kernel(const BatchJob *jobs, unsigned *queue)
 {
     const BatchJob &j = jobs[blockIdx.y];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < j.n_bins; t += gridDim.x * blockDim.x) j.H[t] = 0ull;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *queue = 0u;
+    if (!*j.active) return;  // a frozen lattice keeps its last histogram
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < j.n_bins; t += gridDim.x * blockDim.x) j.H[t] = 0ull;
 }
 
 // kernel tables from the thresholds of every lattice; then advance the iteration
@@ -114,6 +116,7 @@ __global__ void batch_prepare_kernel(const BatchJob *jobs, unsigned *queue)
 __global__ void batch_ktab_kernel(const BatchJob *jobs)
 {
     const BatchJob &j = jobs[blockIdx.y];
+    if (!*j.active) return;
     const int width = j.model == MUCA_ISING ? 5 : 9;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < j.n_bins * width; t += gridDim.x * blockDim.x) {
         const int b = t / width, k = t % width;
@@ -127,6 +130,25 @@ __global__ void batch_ktab_kernel(const BatchJob *jobs)
         j.ktab[t] = v;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *j.iteration += 1u;
+}
+
+// Convergence test of Sec. 3 after the update of iteration `it` (1-based): a lattice
+// whose merged histogram was covered and flat is frozen and records `it`.
+__global__ void batch_converge_kernel(const BatchJob *jobs, int n_jobs, int it)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_jobs) return;
+    const BatchJob &j = jobs[i];
+    if (*j.active && j.stats->flat) {
+        *j.active = 0;
+        *j.conv = it;
+    }
+}
+
+__global__ void batch_fill_kernel(int *x, int n, int v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
 }
 
 struct TuneChoice {
@@ -151,6 +173,8 @@ struct muca_batch {
     int n_units = 0;
     unsigned *d_queue = nullptr;
     uint32_t *d_iter = nullptr;
+    int *d_active = nullptr;  // [n_jobs]: 1 running, 0 frozen (converged)
+    int *d_conv = nullptr;    // [n_jobs]: iteration of convergence, -1 before
     size_t smem = 0;
     int grid = 0, staging = MUCA_STAGING_AUTO, split = 1;
     int max_bins = 0, max_thr = 0, max_ktab = 0;
@@ -219,6 +243,8 @@ int configure(muca_batch *b)
         j.H = c->d_H;
         j.stats = c->d_stats;
         j.iteration = b->d_iter + i;
+        j.active = b->d_active + i;
+        j.conv = b->d_conv + i;
         j.flags = (pl.table_smem ? 4 : 0) | (pl.hist_smem ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
         b->smem = std::max(b->smem, pl.smem_bytes + ws_extra_smem(c->model));
         b->max_bins = std::max(b->max_bins, c->n_bins);
@@ -291,6 +317,8 @@ void free_batch(muca_batch *b)
     if (b->d_units) cudaFree(b->d_units);
     if (b->d_queue) cudaFree(b->d_queue);
     if (b->d_iter) cudaFree(b->d_iter);
+    if (b->d_active) cudaFree(b->d_active);
+    if (b->d_conv) cudaFree(b->d_conv);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -387,11 +415,20 @@ int muca_batch_create(muca_batch **out, const muca_job *jobs, int n_jobs, const 
     }
     if (cudaMalloc(reinterpret_cast<void **>(&b->d_jobs), sizeof(BatchJob) * n_jobs) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&b->d_queue), sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void **>(&b->d_iter), sizeof(uint32_t) * n_jobs) != cudaSuccess) {
+        cudaMalloc(reinterpret_cast<void **>(&b->d_iter), sizeof(uint32_t) * n_jobs) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&b->d_active), sizeof(int) * n_jobs) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&b->d_conv), sizeof(int) * n_jobs) != cudaSuccess) {
         cudaGetLastError();
         free_batch(b);
         return fail(MUCA_ERR_OOM, "batch tables");
     }
+    batch_fill_kernel<<<(n_jobs + 255) / 256, 256, 0, b->stream>>>(b->d_active, n_jobs, 1);
+    batch_fill_kernel<<<(n_jobs + 255) / 256, 256, 0, b->stream>>>(b->d_conv, n_jobs, -1);
+    if (cudaGetLastError() != cudaSuccess) {
+        free_batch(b);
+        return fail(MUCA_ERR_CUDA, "batch flags");
+    }
+    note_launches(2);
     int rc = configure(b);
     if (rc) {
         free_batch(b);
@@ -415,10 +452,11 @@ muca_ctx *muca_batch_job(muca_batch *b, int j)
     return b->ctx[j];
 }
 
-int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_graph)
+namespace {
+// Before a call that queues iterations: sweep launches per iteration, pending tables
+// of individual contexts, and the iteration counters of the random streams.
+int begin_iterations(muca_batch *b, int n_sweeps)
 {
-    if (!b) return fail(MUCA_ERR_ARG, "null batch");
-    if (n_iterations < 1 || n_sweeps < 1) return fail(MUCA_ERR_ARG, "need n_iterations >= 1 and n_sweeps >= 1");
     // uint32 block histograms: 32 chains x sweeps x sites per launch below 2^31
     long long vmax = 0;
     for (muca_ctx *c : b->ctx) vmax = std::max<long long>(vmax, c->V);
@@ -439,6 +477,16 @@ int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_gr
     MUCA_CUDA_TRY(cudaMemcpyAsync(b->d_iter, it.data(), sizeof(uint32_t) * b->n_jobs, cudaMemcpyHostToDevice,
                                   b->stream));
     MUCA_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return MUCA_OK;
+}
+}  // namespace
+
+int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_graph)
+{
+    if (!b) return fail(MUCA_ERR_ARG, "null batch");
+    if (n_iterations < 1 || n_sweeps < 1) return fail(MUCA_ERR_ARG, "need n_iterations >= 1 and n_sweeps >= 1");
+    int rc0 = begin_iterations(b, n_sweeps);
+    if (rc0) return rc0;
     if (use_graph) {
         if (!b->gexec || b->g_iters != n_iterations || b->g_sweeps != n_sweeps) {
             drop_graph(b);
@@ -474,6 +522,54 @@ int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_gr
         c->lnw_version += (uint64_t)n_iterations;
         c->ktab_dirty = 0;
     }
+    return MUCA_OK;
+}
+
+int muca_batch_converge(muca_batch *b, int n_sweeps, int max_iterations, int *n_iter_out)
+{
+    if (!b) return fail(MUCA_ERR_ARG, "null batch");
+    if (n_sweeps < 1 || max_iterations < 1) return fail(MUCA_ERR_ARG, "need n_sweeps >= 1 and max_iterations >= 1");
+    int rc = begin_iterations(b, n_sweeps);
+    if (rc) return rc;
+    const int nb = (b->n_jobs + 255) / 256;
+    batch_fill_kernel<<<nb, 256, 0, b->stream>>>(b->d_active, b->n_jobs, 1);
+    batch_fill_kernel<<<nb, 256, 0, b->stream>>>(b->d_conv, b->n_jobs, -1);
+    MUCA_CUDA_TRY(cudaGetLastError());
+    note_launches(2);
+    std::vector<int> conv(b->n_jobs, -1);
+    // Iterations are queued in chunks and the host looks at the flags between chunks; a
+    // lattice freezes on the device in the iteration it converges, so the chunk size
+    // changes nothing but how soon the call returns.
+    int done = 0, chunk = 1;
+    while (done < max_iterations) {
+        const int n = std::min(chunk, max_iterations - done);
+        for (int i = 0; i < n; ++i) {
+            if ((rc = enqueue_iteration(b, n_sweeps))) return rc;
+            batch_converge_kernel<<<nb, 256, 0, b->stream>>>(b->d_jobs, b->n_jobs, done + i + 1);
+            MUCA_CUDA_TRY(cudaGetLastError());
+            note_launches(1);
+        }
+        done += n;
+        MUCA_CUDA_TRY(cudaMemcpyAsync(conv.data(), b->d_conv, sizeof(int) * b->n_jobs, cudaMemcpyDeviceToHost,
+                                      b->stream));
+        MUCA_CUDA_TRY(cudaStreamSynchronize(b->stream));
+        if (std::all_of(conv.begin(), conv.end(), [](int v) { return v >= 0; })) break;
+        chunk = std::min(chunk * 2, 8);
+    }
+    // host-side state of every context: the iterations it actually ran
+    for (int i = 0; i < b->n_jobs; ++i) {
+        muca_ctx *c = b->ctx[i];
+        const int ran = conv[i] >= 0 ? conv[i] : done;
+        c->iteration += (uint32_t)ran;
+        c->have_hist = 0;
+        c->lnw_version += (uint64_t)ran;
+        c->ktab_dirty = 0;
+        if (n_iter_out) n_iter_out[i] = conv[i];
+    }
+    batch_fill_kernel<<<nb, 256, 0, b->stream>>>(b->d_active, b->n_jobs, 1);
+    MUCA_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+    MUCA_CUDA_TRY(cudaStreamSynchronize(b->stream));
     return MUCA_OK;
 }
 

@@ -306,6 +306,26 @@ int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out)
     return MUCA_OK;
 }
 
+int muca_converge(muca_ctx *ctx, int n_sweeps, int max_iterations, int *n_iter_out, muca_iter_stats *last)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (n_sweeps < 1 || max_iterations < 1) return fail(MUCA_ERR_ARG, "need n_sweeps >= 1 and max_iterations >= 1");
+    muca_iter_stats st{};
+    int conv = -1;
+    for (int it = 1; it <= max_iterations; ++it) {
+        if ((rc = muca_iterate(ctx, n_sweeps, nullptr))) return rc;
+        if ((rc = muca_update_weights(ctx, &st))) return rc;
+        if (st.flat) {
+            conv = it;
+            break;
+        }
+    }
+    if (n_iter_out) *n_iter_out = conv;
+    if (last) *last = st;
+    return MUCA_OK;
+}
+
 int muca_thermalize(muca_ctx *ctx, int n_sweeps)
 {
     int rc;

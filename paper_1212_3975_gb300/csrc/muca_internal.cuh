@@ -117,6 +117,8 @@ struct BatchJob {
     muca_iter_stats *stats;
     uint32_t *iteration;        // device counter of weight iterations (counter word 2)
     int flags;                  // staging of the sweep body: 4 table, 2 histogram, 1 lattice in smem
+    int *active;                // 0: the lattice is frozen (converged) and every batch kernel skips it
+    int *conv;                  // iteration at which the lattice converged, -1 before
 };
 
 }  // namespace muca

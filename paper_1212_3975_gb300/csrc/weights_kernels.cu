@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(1024) update_kernel(double *lnw, double *P, do
 __global__ void __launch_bounds__(1024) update_batch_kernel(const BatchJob *jobs)
 {
     const BatchJob &j = jobs[blockIdx.x];
+    if (!*j.active) return;  // converged lattice: frozen
     update_body(j.lnw, j.P, j.wscratch, j.H, j.acc, j.n_bins, j.accumulated, j.width, j.stats);
 }
 
@@ -223,6 +224,7 @@ __global__ void __launch_bounds__(1024) update_batch_kernel(const BatchJob *jobs
 __global__ void thresholds_batch_kernel(const BatchJob *jobs)
 {
     const BatchJob &j = jobs[blockIdx.y];
+    if (!*j.active) return;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < j.n_bins * j.n_de; t += gridDim.x * blockDim.x) {
         const int b = t / j.n_de, col = t % j.n_de;
         const int bp = b + bin_delta(j.model, col);

@@ -1,0 +1,148 @@
+"""The performance study of Sec. 4, with chains in the role of cores.
+
+For each lattice size L and number of chains p, parallel MUCA runs start from
+ln W = 0 and iterate until the merged histogram is covered and flat (Sec. 3); the
+mean number of iterations over independent seeds is N_iter(M, p).  Following Sec. 4:
+
+* the total number of sweeps to convergence is N_iter M p, and its minimum over the
+  sweeps per iteration and chain M is M_opt(L, p) (Fig. 2, left);
+* M_opt(L, p) = M_1(L) / p is fitted for each L (Fig. 2, right) and
+  M_1(L) = a L^(2+b) over L (Fig. 3; Eq. 7 gives a = 5.7(5), b = 0.51(4) for Ising and
+  a = 24(4), b = 0.67(6) for 8-Potts);
+* the statistical speedup S*_p = [N_iter M_opt(L,1)]_1 / [N_iter M_opt(L,p)]_p compares
+  the sweeps per chain to convergence with p chains and with one.
+
+The runs go through the batched C entry point muca_batch_converge (every lattice of a
+batch freezes in the iteration it converges); this module only arranges jobs and does
+the least-squares fits on the host.
+"""
+import math
+
+import numpy as np
+
+from . import MucaBatch
+
+ISING, POTTS = 0, 1
+# Eq. 7: M_opt(L, p) = a L^(2+b) / p
+EQ7 = {ISING: (5.7, 0.51), POTTS: (24.0, 0.67)}
+
+
+def eq7_m_opt(model, L, p):
+    """M_opt(L, p) of Eq. 7 (the paper's fit on its own implementation)."""
+    a, b = EQ7[model]
+    return a * L ** (2.0 + b) / p
+
+
+def n_iter_runs(model, L, p_list, M, seeds, max_iterations, seed0=1):
+    """N_iter of every (p, seed) at M sweeps per iteration and chain, from one batch.
+
+    Returns {p: array of N_iter over the seeds} (-1 where a run did not converge
+    within max_iterations)."""
+    q = 2 if model == ISING else 8
+    jobs = [(model, L, q, int(p), seed0 + 1000 * i + s) for i, p in enumerate(p_list) for s in range(seeds)]
+    b = MucaBatch(jobs)
+    try:
+        n = b.converge(int(M), max_iterations)
+    finally:
+        b.close()
+    return {int(p): n[i * seeds:(i + 1) * seeds].copy() for i, p in enumerate(p_list)}
+
+
+def mean_n_iter(runs):
+    """Mean N_iter over seeds; infinite when any run failed to converge."""
+    runs = np.asarray(runs)
+    return math.inf if (runs < 0).any() else float(runs.mean())
+
+
+def m_opt_from_scan(M_list, totals):
+    """M_opt as the minimum of the total sweeps N_iter M p over the scanned M (Sec. 4,
+    Fig. 2 left), refined by a parabola in log M through the smallest point and its two
+    neighbours when the minimum is interior.  Returns (M_opt, total at the minimum)."""
+    M = np.asarray(M_list, dtype=np.float64)
+    t = np.asarray(totals, dtype=np.float64)
+    order = np.argsort(M)
+    M, t = M[order], t[order]
+    finite = np.isfinite(t)
+    if not finite.any():
+        return math.nan, math.inf
+    i = int(np.argmin(np.where(finite, t, np.inf)))
+    if 0 < i < len(M) - 1 and finite[i - 1] and finite[i + 1]:
+        x = np.log(M[i - 1:i + 2])
+        y = t[i - 1:i + 2]
+        c2, c1, c0 = np.polyfit(x, y, 2)
+        if c2 > 0:
+            xm = -c1 / (2 * c2)
+            if x[0] <= xm <= x[2]:
+                return float(math.exp(xm)), float(c0 + c1 * xm + c2 * xm * xm)
+    return float(M[i]), float(t[i])
+
+
+def fit_m1(p_list, m_opt):
+    """M_1 of M_opt(p) = M_1 / p: least squares in log space with the exponent fixed
+    at -1 (Sec. 4), i.e. the geometric mean of M_opt(p) p."""
+    p = np.asarray(p_list, dtype=np.float64)
+    m = np.asarray(m_opt, dtype=np.float64)
+    ok = np.isfinite(m) & (m > 0)
+    return float(np.exp(np.mean(np.log(m[ok] * p[ok]))))
+
+
+def fit_power(L_list, m1):
+    """(a, b) of M_1(L) = a L^(2+b): linear least squares of log(M_1 / L^2) on log L."""
+    L = np.asarray(L_list, dtype=np.float64)
+    m = np.asarray(m1, dtype=np.float64)
+    b, loga = np.polyfit(np.log(L), np.log(m / L ** 2), 1)
+    return float(math.exp(loga)), float(b)
+
+
+def statistical_speedup(sweeps_per_chain):
+    """S*_p = [N_iter M]_1 / [N_iter M]_p from {p: mean sweeps per chain to convergence}."""
+    base = sweeps_per_chain[1]
+    return {p: base / v for p, v in sweeps_per_chain.items()}
+
+
+def m_scan(model, L, p_list, M_factors, seeds, max_iterations, M_center=None, seed0=1):
+    """N_iter over a grid of M for every p.  The grid is geometric around M_center(p)
+    (default: Eq. 7's M_opt(L, p)); runs sharing an M share one batch.
+
+    Returns {p: (M list, mean N_iter list, total sweeps N_iter M p list)}."""
+    if M_center is None:
+        M_center = lambda p: eq7_m_opt(model, L, p)  # noqa: E731
+    grid = {int(p): sorted({max(1, int(round(M_center(p) * f))) for f in M_factors}) for p in p_list}
+    by_M = {}
+    for p, Ms in grid.items():
+        for M in Ms:
+            by_M.setdefault(M, []).append(p)
+    res = {p: {} for p in grid}
+    for M, ps in sorted(by_M.items()):
+        runs = n_iter_runs(model, L, ps, M, seeds, max_iterations, seed0)
+        for p in ps:
+            res[p][M] = mean_n_iter(runs[p])
+    out = {}
+    for p in grid:
+        Ms = sorted(res[p])
+        n = [res[p][M] for M in Ms]
+        out[p] = (Ms, n, [v * M * p for v, M in zip(n, Ms)])
+    return out
+
+
+def speedup_from_scan(scan):
+    """S*_p from the minima of an M scan: the sweeps per chain to convergence at the
+    optimal M of each p are min_M(N_iter M p) / p, so
+    S*_p = min_total(1) / (min_total(p) / p)."""
+    best = {p: m_opt_from_scan(Ms, tot) for p, (Ms, n, tot) in scan.items()}
+    per_chain = {p: t / p for p, (m, t) in best.items()}
+    return {p: m for p, (m, t) in best.items()}, per_chain, (statistical_speedup(per_chain) if 1 in per_chain
+                                                            else {})
+
+
+def speedup_runs(model, L, p_list, m1, seeds, max_iterations, seed0=7):
+    """Mean sweeps per chain to convergence N_iter M_opt(L, p) at M_opt = M_1 / p for
+    every p (one batch per p), and S*_p."""
+    per_chain = {}
+    n_iter = {}
+    for p in p_list:
+        M = max(1, int(round(m1 / p)))
+        runs = n_iter_runs(model, L, [p], M, seeds, max_iterations, seed0)[int(p)]
+        n_iter[int(p)] = mean_n_iter(runs)
+        per_chain[int(p)] = n_iter[int(p)] * M
+    return n_iter, per_chain, statistical_speedup(per_chain) if 1 in per_chain else {}
