@@ -372,19 +372,34 @@ def statistical_study():
     M on a geometric grid around Eq. 7's M_opt(8, p), runs capped at 400 iterations.
     M_opt(p) is the minimum of N_iter M p; S*_p comes from the same minima."""
     from paper_1212_3975_gb300 import study
+    fin = lambda x: None if not math.isfinite(x) else round(float(x), 3)  # noqa: E731
     ps = [1, 2, 4, 8, 16, 32]
     factors = [0.5, 0.7, 1.0, 1.4, 2.0, 2.8, 4.0]
     t0 = time.perf_counter()
     scan = study.m_scan(study.ISING, 8, ps, factors, 10, 400)
     m_opt, per_chain, S = study.speedup_from_scan(scan)
     m1 = study.fit_m1(ps, [m_opt[p] for p in ps])
-    fin = lambda x: None if not math.isfinite(x) else round(float(x), 3)  # noqa: E731
+    # intermediate thermalisation between iterations (Sec. 4): 8-Potts 8x8, p = 16 chains,
+    # M = Eq. 7's M_opt(8, 16), 16 seeds, at most 200 iterations
+    therm = {}
+    p = 16
+    M = int(round(study.eq7_m_opt(study.POTTS, 8, p)))
+    for T in (0, M // 4, M):
+        runs = study.n_iter_runs(study.POTTS, 8, [p], M, 16, 200, seed0=11, therm_sweeps=T)[p]
+        ok = runs[runs > 0]
+        therm["T%d" % T] = {
+            "converged": "%d/%d" % (len(ok), len(runs)),
+            "median_n_iter": fin(float(np.median(ok))) if len(ok) else None,
+            "median_sweeps_per_chain": fin(float(np.median(ok * M + (ok - 1) * T))) if len(ok) else None}
     return {
         "workload": "8x8 Ising, p in 1..32, 10 seeds per (p, M), M grid x{0.5..4} around Eq. 7, <= 400 iterations",
         "M_opt": {str(p): fin(m_opt[p]) for p in ps},
         "M1_fit": round(m1, 1), "M1_eq7": round(study.eq7_m_opt(study.ISING, 8, 1), 1),
         "sweeps_per_chain_to_convergence": {str(p): fin(per_chain[p]) for p in ps},
         "S_star": {str(p): fin(S[p]) for p in ps},
+        "intermediate_thermalization": {"workload": "8-Potts 8x8, p = 16, M = Eq. 7 M_opt(8, 16) = %d, T sweeps "
+                                                    "after every unconverged update, 16 seeds, <= 200 iterations" % M,
+                                        **therm},
         "seconds": round(time.perf_counter() - t0, 2),
     }
 

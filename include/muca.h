@@ -138,11 +138,16 @@ int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out);
  * muca_iterate(n_sweeps) + muca_update_weights, repeated until the merged histogram
  * of an iteration is covered and flat, or max_iterations were run.  The update of
  * the converged iteration is applied, so the context holds the weights that follow
- * it.  *n_iter_out (host, may be NULL) = the number of iterations run when the last
- * one converged (the paper's N_iter), -1 if none did; *last (host, may be NULL) = the
+ * it.  therm_sweeps > 0: after every update that did not converge (and is not the
+ * last allowed iteration) the chains are thermalised for that many sweeps with the
+ * new weights (muca_thermalize), the intermediate thermalisation of Sec. 4.
+ * *n_iter_out (host, may be NULL) = the number of iterations run when the last one
+ * converged (the paper's N_iter), -1 if none did; *last (host, may be NULL) = the
  * statistics of the last iteration.  Synchronises once per iteration.
- * Errors: MUCA_ERR_ARG (n_sweeps < 1 or max_iterations < 1), MUCA_ERR_CUDA. */
-int muca_converge(muca_ctx *ctx, int n_sweeps, int max_iterations, int *n_iter_out, muca_iter_stats *last);
+ * Errors: MUCA_ERR_ARG (n_sweeps < 1, therm_sweeps < 0 or max_iterations < 1),
+ * MUCA_ERR_CUDA. */
+int muca_converge(muca_ctx *ctx, int n_sweeps, int therm_sweeps, int max_iterations, int *n_iter_out,
+                  muca_iter_stats *last);
 
 /* Thermalise every chain with the current weights for n_sweeps sweeps (Sec. 3:
  * "thermalized again" before production); nothing is recorded. */
@@ -246,13 +251,14 @@ int muca_batch_destroy(muca_batch *b);
 int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_graph);
 
 /* Weight iterations of every lattice until each converges (as muca_converge on each
- * context, and bit-identical to it): a lattice whose merged histogram is covered and
- * flat freezes in that iteration -- no further sweeps, updates or counter advances --
- * while the others go on, up to max_iterations.  n_iter_out[n_jobs] (host, may be
- * NULL) receives each lattice's N_iter, -1 for one that did not converge.  Afterwards
- * every lattice runs again in later calls.  Synchronises every few iterations.
+ * context with the same arguments, and bit-identical to it): a lattice whose merged
+ * histogram is covered and flat freezes in that iteration -- no further sweeps,
+ * thermalisation, updates or counter advances -- while the others go on, up to
+ * max_iterations.  n_iter_out[n_jobs] (host, may be NULL) receives each lattice's
+ * N_iter, -1 for one that did not converge.  Afterwards every lattice runs again in
+ * later calls.  Synchronises every few iterations.
  * Errors: MUCA_ERR_ARG, MUCA_ERR_CUDA. */
-int muca_batch_converge(muca_batch *b, int n_sweeps, int max_iterations, int *n_iter_out);
+int muca_batch_converge(muca_batch *b, int n_sweeps, int therm_sweeps, int max_iterations, int *n_iter_out);
 
 /* The context of job j (owned by the batch; use it for state access). */
 muca_ctx *muca_batch_job(muca_batch *b, int j);

@@ -106,17 +106,21 @@ class MucaOracle:
         self.thr = weights.thresholds(self.model, self.L, self.lnw, self.acc)
         return stats
 
-    def converge(self, n_sweeps, max_iterations):
+    def converge(self, n_sweeps, max_iterations, therm_sweeps=0):
         """Weight iterations until convergence (Sec. 3): sweeps of one iteration, then the
         update; stop after the first iteration whose histogram (before its update) is
-        covered and flat.  Returns (N_iter, its statistics); N_iter = -1 if no
-        iteration up to max_iterations converged."""
+        covered and flat.  With therm_sweeps > 0 the chains are thermalised with the new
+        weights after every update that did not converge, unless it was the last allowed
+        iteration (the intermediate thermalisation of Sec. 4).  Returns (N_iter, its
+        statistics); N_iter = -1 if no iteration up to max_iterations converged."""
         stats = None
         for it in range(1, max_iterations + 1):
             self.iterate(n_sweeps)
             stats = self.update_weights()
             if stats["flat"]:
                 return it, stats
+            if therm_sweeps > 0 and it < max_iterations:
+                self.thermalize(therm_sweeps)
         return -1, stats
 
     def set_lnw(self, lnw):

@@ -94,12 +94,14 @@ class Muca:
         check(lib().muca_update_weights(self._h, ctypes.byref(st)))
         return st.as_dict()
 
-    def converge(self, n_sweeps, max_iterations):
-        """Weight iterations until the histogram is covered and flat; returns
-        (N_iter or -1, statistics of the last iteration)."""
+    def converge(self, n_sweeps, max_iterations, therm_sweeps=0):
+        """Weight iterations until the histogram is covered and flat (with therm_sweeps
+        of intermediate thermalisation after every update that did not converge);
+        returns (N_iter or -1, statistics of the last iteration)."""
         n = ctypes.c_int(-1)
         st = MucaIterStats()
-        check(lib().muca_converge(self._h, n_sweeps, max_iterations, ctypes.byref(n), ctypes.byref(st)))
+        check(lib().muca_converge(self._h, n_sweeps, therm_sweeps, max_iterations, ctypes.byref(n),
+                                  ctypes.byref(st)))
         return n.value, st.as_dict()
 
     def thermalize(self, n_sweeps):
@@ -231,11 +233,11 @@ class MucaBatch:
     def iterate(self, n_iterations, n_sweeps, graph=True):
         check(lib().muca_batch_iterate(self._h, n_iterations, n_sweeps, 1 if graph else 0))
 
-    def converge(self, n_sweeps, max_iterations):
+    def converge(self, n_sweeps, max_iterations, therm_sweeps=0):
         """Iterate every lattice until it converges (frozen from then on); returns
         N_iter per lattice (int32, -1 where max_iterations was reached)."""
         out = np.full(len(self.jobs), -1, dtype=np.int32)
-        check(lib().muca_batch_converge(self._h, n_sweeps, max_iterations, _ptr(out)))
+        check(lib().muca_batch_converge(self._h, n_sweeps, therm_sweeps, max_iterations, _ptr(out)))
         return out
 
     def autotune(self, n_sweeps, cache_path=None):

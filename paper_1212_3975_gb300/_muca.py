@@ -64,7 +64,7 @@ _SIGS = {
     "muca_iterate": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "muca_update_weights": (ctypes.c_int, [_P, ctypes.POINTER(MucaIterStats)]),
     "muca_thermalize": (ctypes.c_int, [_P, ctypes.c_int]),
-    "muca_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+    "muca_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(MucaIterStats)]),
     "muca_produce": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "muca_reset_samples": (ctypes.c_int, [_P]),
@@ -83,7 +83,7 @@ _SIGS = {
                                          ctypes.POINTER(MucaConfig), _P]),
     "muca_batch_destroy": (ctypes.c_int, [_P]),
     "muca_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-    "muca_batch_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "muca_batch_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "muca_batch_job": (_P, [_P, ctypes.c_int]),
     "muca_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
     "muca_save": (ctypes.c_int, [_P, ctypes.c_char_p]),

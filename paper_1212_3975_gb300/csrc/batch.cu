@@ -26,7 +26,7 @@ struct BatchUnit {
     int job, cblk;
 };
 
-__device__ __forceinline__ SweepArgs batch_args(const BatchJob &j, int n_sweeps, uint32_t sweep0)
+__device__ __forceinline__ SweepArgs batch_args(const BatchJob &j, int n_sweeps, uint32_t sweep0, bool therm)
 {
     SweepArgs a;
     a.lat = j.lat;
@@ -47,39 +47,43 @@ __device__ __forceinline__ SweepArgs batch_args(const BatchJob &j, int n_sweeps,
     a.lat_words = j.lat_words;
     a.n_bins = j.n_bins;
     a.n_sweeps = n_sweeps;
-    a.sweep0 = sweep0;
-    a.iteration = *j.iteration;
-    a.ctr3 = j.ctr3_iter;
+    // weight iterations: counter words (sweep in the iteration, iteration, phase 1);
+    // thermalisation: (running sweep count, 0, phase 2), as the standalone calls
+    a.sweep0 = therm ? *j.therm + sweep0 : sweep0;
+    a.iteration = therm ? 0u : *j.iteration;
+    a.ctr3 = therm ? j.ctr3_therm : j.ctr3_iter;
     a.key0 = j.key0;
     a.rec_stride = j.p;
     return a;
 }
 
-template <int MODEL, bool T, bool H, bool Lt>
+template <int MODEL, bool HIST, bool T, bool H, bool Lt>
 __device__ __forceinline__ void body(const SweepArgs &a, int cblk, uint32_t *smem)
 {
     if (MODEL == MUCA_ISING)
-        ising_ws_body<true, false, T, H, Lt>(a, cblk, smem);
+        ising_ws_body<HIST, false, T, H && HIST, Lt>(a, cblk, smem);
     else
-        potts_ws_body<true, false, T, H, Lt>(a, cblk, smem);
+        potts_ws_body<HIST, false, T, H && HIST, Lt>(a, cblk, smem);
 }
 
-template <int MODEL>
+template <int MODEL, bool HIST>
 __device__ __forceinline__ void run_unit(const SweepArgs &a, int flags, int cblk, uint32_t *smem)
 {
     switch (flags) {
-    case 0: body<MODEL, false, false, false>(a, cblk, smem); break;
-    case 1: body<MODEL, false, false, true>(a, cblk, smem); break;
-    case 2: body<MODEL, false, true, false>(a, cblk, smem); break;
-    case 3: body<MODEL, false, true, true>(a, cblk, smem); break;
-    case 4: body<MODEL, true, false, false>(a, cblk, smem); break;
-    case 5: body<MODEL, true, false, true>(a, cblk, smem); break;
-    case 6: body<MODEL, true, true, false>(a, cblk, smem); break;
-    default: body<MODEL, true, true, true>(a, cblk, smem); break;
+    case 0: body<MODEL, HIST, false, false, false>(a, cblk, smem); break;
+    case 1: body<MODEL, HIST, false, false, true>(a, cblk, smem); break;
+    case 2: body<MODEL, HIST, false, true, false>(a, cblk, smem); break;
+    case 3: body<MODEL, HIST, false, true, true>(a, cblk, smem); break;
+    case 4: body<MODEL, HIST, true, false, false>(a, cblk, smem); break;
+    case 5: body<MODEL, HIST, true, false, true>(a, cblk, smem); break;
+    case 6: body<MODEL, HIST, true, true, false>(a, cblk, smem); break;
+    default: body<MODEL, HIST, true, true, true>(a, cblk, smem); break;
     }
 }
 
-// Persistent sweep kernel of one weight iteration (or part of it).
+// Persistent sweep kernel of one weight iteration (or part of it); THERM: sweeps of
+// an intermediate thermalisation (no histogram).
+template <bool THERM>
 __global__ void __launch_bounds__(128) batch_sweep_kernel(const BatchJob *jobs, const BatchUnit *units, int n_units,
                                                           unsigned *queue, int n_sweeps, uint32_t sweep0)
 {
@@ -94,11 +98,11 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const BatchJob *jobs, 
         const BatchUnit un = units[u];
         const BatchJob &j = jobs[un.job];
         if (!*j.active) continue;  // converged: frozen
-        const SweepArgs a = batch_args(j, n_sweeps, sweep0);
+        const SweepArgs a = batch_args(j, n_sweeps, sweep0, THERM);
         if (j.model == MUCA_ISING)
-            run_unit<MUCA_ISING>(a, j.flags, un.cblk, smem);
+            run_unit<MUCA_ISING, !THERM>(a, j.flags, un.cblk, smem);
         else
-            run_unit<MUCA_POTTS>(a, j.flags, un.cblk, smem);
+            run_unit<MUCA_POTTS, !THERM>(a, j.flags, un.cblk, smem);
     }
 }
 
@@ -145,6 +149,13 @@ __global__ void batch_converge_kernel(const BatchJob *jobs, int n_jobs, int it)
     }
 }
 
+// after a thermalisation pass: advance the sweep counters of the running lattices
+__global__ void batch_therm_advance_kernel(const BatchJob *jobs, int n_jobs, int n_sweeps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_jobs && *jobs[i].active) *jobs[i].therm += (uint32_t)n_sweeps;
+}
+
 __global__ void batch_fill_kernel(int *x, int n, int v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,6 +186,7 @@ struct muca_batch {
     uint32_t *d_iter = nullptr;
     int *d_active = nullptr;  // [n_jobs]: 1 running, 0 frozen (converged)
     int *d_conv = nullptr;    // [n_jobs]: iteration of convergence, -1 before
+    uint32_t *d_therm = nullptr;  // [n_jobs]: thermalisation sweep counters
     size_t smem = 0;
     int grid = 0, staging = MUCA_STAGING_AUTO, split = 1;
     int max_bins = 0, max_thr = 0, max_ktab = 0;
@@ -245,6 +257,8 @@ int configure(muca_batch *b)
         j.iteration = b->d_iter + i;
         j.active = b->d_active + i;
         j.conv = b->d_conv + i;
+        j.ctr3_therm = ((uint32_t)(c->seed >> 32) << 2) | kPhaseThermalize;
+        j.therm = b->d_therm + i;
         j.flags = (pl.table_smem ? 4 : 0) | (pl.hist_smem ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
         b->smem = std::max(b->smem, pl.smem_bytes + ws_extra_smem(c->model));
         b->max_bins = std::max(b->max_bins, c->n_bins);
@@ -273,7 +287,10 @@ int configure(muca_batch *b)
                                   b->stream));
     MUCA_CUDA_TRY(cudaStreamSynchronize(b->stream));
     if (b->smem > 227 * 1024) return fail(MUCA_ERR_ARG, "batched staging exceeds shared memory");
-    MUCA_CUDA_TRY(cudaFuncSetAttribute(batch_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    MUCA_CUDA_TRY(
+        cudaFuncSetAttribute(batch_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    MUCA_CUDA_TRY(
+        cudaFuncSetAttribute(batch_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     if (b->grid <= 0) b->grid = std::min(b->n_units, sm_count());
     drop_graph(b);
     return MUCA_OK;
@@ -293,8 +310,8 @@ int enqueue_iteration(muca_batch *b, int n_sweeps)
         } else {
             MUCA_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
         }
-        batch_sweep_kernel<<<b->grid, 128, b->smem, b->stream>>>(b->d_jobs, b->d_units, b->n_units, b->d_queue, s1 - s0,
-                                                                  (uint32_t)s0);
+        batch_sweep_kernel<false><<<b->grid, 128, b->smem, b->stream>>>(b->d_jobs, b->d_units, b->n_units, b->d_queue,
+                                                                         s1 - s0, (uint32_t)s0);
         MUCA_CUDA_TRY(cudaGetLastError());
         note_launches(1);
     }
@@ -319,6 +336,7 @@ void free_batch(muca_batch *b)
     if (b->d_iter) cudaFree(b->d_iter);
     if (b->d_active) cudaFree(b->d_active);
     if (b->d_conv) cudaFree(b->d_conv);
+    if (b->d_therm) cudaFree(b->d_therm);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -417,7 +435,8 @@ int muca_batch_create(muca_batch **out, const muca_job *jobs, int n_jobs, const 
         cudaMalloc(reinterpret_cast<void **>(&b->d_queue), sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&b->d_iter), sizeof(uint32_t) * n_jobs) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&b->d_active), sizeof(int) * n_jobs) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void **>(&b->d_conv), sizeof(int) * n_jobs) != cudaSuccess) {
+        cudaMalloc(reinterpret_cast<void **>(&b->d_conv), sizeof(int) * n_jobs) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&b->d_therm), sizeof(uint32_t) * n_jobs) != cudaSuccess) {
         cudaGetLastError();
         free_batch(b);
         return fail(MUCA_ERR_OOM, "batch tables");
@@ -464,8 +483,9 @@ int begin_iterations(muca_batch *b, int n_sweeps)
         b->split *= 2;
         drop_graph(b);
     }
-    // pending threshold tables of individual contexts, and iteration counters
-    std::vector<uint32_t> it(b->n_jobs);
+    // pending threshold tables of individual contexts, iteration and thermalisation
+    // counters
+    std::vector<uint32_t> it(b->n_jobs), th(b->n_jobs);
     for (int i = 0; i < b->n_jobs; ++i) {
         muca_ctx *c = b->ctx[i];
         if (c->ktab_dirty) {
@@ -473,8 +493,11 @@ int begin_iterations(muca_batch *b, int n_sweeps)
             if (rc) return rc;
         }
         it[i] = c->iteration;
+        th[i] = c->sweeps_therm;
     }
     MUCA_CUDA_TRY(cudaMemcpyAsync(b->d_iter, it.data(), sizeof(uint32_t) * b->n_jobs, cudaMemcpyHostToDevice,
+                                  b->stream));
+    MUCA_CUDA_TRY(cudaMemcpyAsync(b->d_therm, th.data(), sizeof(uint32_t) * b->n_jobs, cudaMemcpyHostToDevice,
                                   b->stream));
     MUCA_CUDA_TRY(cudaStreamSynchronize(b->stream));
     return MUCA_OK;
@@ -525,10 +548,32 @@ int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_gr
     return MUCA_OK;
 }
 
-int muca_batch_converge(muca_batch *b, int n_sweeps, int max_iterations, int *n_iter_out)
+namespace {
+// Thermalisation sweeps of every running lattice (no histogram), in launches that
+// keep the uint32 block histogram bound of the iteration launches.
+int enqueue_thermalization(muca_batch *b, int n_sweeps)
+{
+    const int split = std::max(1, std::min(b->split, n_sweeps));
+    for (int s = 0; s < split; ++s) {
+        const int s0 = (int)((long long)n_sweeps * s / split), s1 = (int)((long long)n_sweeps * (s + 1) / split);
+        MUCA_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
+        batch_sweep_kernel<true><<<b->grid, 128, b->smem, b->stream>>>(b->d_jobs, b->d_units, b->n_units, b->d_queue,
+                                                                        s1 - s0, (uint32_t)s0);
+        MUCA_CUDA_TRY(cudaGetLastError());
+        note_launches(1);
+    }
+    batch_therm_advance_kernel<<<(b->n_jobs + 255) / 256, 256, 0, b->stream>>>(b->d_jobs, b->n_jobs, n_sweeps);
+    MUCA_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+    return MUCA_OK;
+}
+}  // namespace
+
+int muca_batch_converge(muca_batch *b, int n_sweeps, int therm_sweeps, int max_iterations, int *n_iter_out)
 {
     if (!b) return fail(MUCA_ERR_ARG, "null batch");
-    if (n_sweeps < 1 || max_iterations < 1) return fail(MUCA_ERR_ARG, "need n_sweeps >= 1 and max_iterations >= 1");
+    if (n_sweeps < 1 || max_iterations < 1 || therm_sweeps < 0)
+        return fail(MUCA_ERR_ARG, "need n_sweeps >= 1, therm_sweeps >= 0 and max_iterations >= 1");
     int rc = begin_iterations(b, n_sweeps);
     if (rc) return rc;
     const int nb = (b->n_jobs + 255) / 256;
@@ -548,6 +593,9 @@ int muca_batch_converge(muca_batch *b, int n_sweeps, int max_iterations, int *n_
             batch_converge_kernel<<<nb, 256, 0, b->stream>>>(b->d_jobs, b->n_jobs, done + i + 1);
             MUCA_CUDA_TRY(cudaGetLastError());
             note_launches(1);
+            // intermediate thermalisation before the next iteration of the running lattices
+            if (therm_sweeps > 0 && done + i + 1 < max_iterations && (rc = enqueue_thermalization(b, therm_sweeps)))
+                return rc;
         }
         done += n;
         MUCA_CUDA_TRY(cudaMemcpyAsync(conv.data(), b->d_conv, sizeof(int) * b->n_jobs, cudaMemcpyDeviceToHost,
@@ -561,6 +609,7 @@ int muca_batch_converge(muca_batch *b, int n_sweeps, int max_iterations, int *n_
         muca_ctx *c = b->ctx[i];
         const int ran = conv[i] >= 0 ? conv[i] : done;
         c->iteration += (uint32_t)ran;
+        c->sweeps_therm += (uint32_t)therm_sweeps * (uint32_t)(conv[i] >= 0 ? ran - 1 : std::min(done, max_iterations - 1));
         c->have_hist = 0;
         c->lnw_version += (uint64_t)ran;
         c->ktab_dirty = 0;

@@ -306,11 +306,13 @@ int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out)
     return MUCA_OK;
 }
 
-int muca_converge(muca_ctx *ctx, int n_sweeps, int max_iterations, int *n_iter_out, muca_iter_stats *last)
+int muca_converge(muca_ctx *ctx, int n_sweeps, int therm_sweeps, int max_iterations, int *n_iter_out,
+                  muca_iter_stats *last)
 {
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
-    if (n_sweeps < 1 || max_iterations < 1) return fail(MUCA_ERR_ARG, "need n_sweeps >= 1 and max_iterations >= 1");
+    if (n_sweeps < 1 || max_iterations < 1 || therm_sweeps < 0)
+        return fail(MUCA_ERR_ARG, "need n_sweeps >= 1, therm_sweeps >= 0 and max_iterations >= 1");
     muca_iter_stats st{};
     int conv = -1;
     for (int it = 1; it <= max_iterations; ++it) {
@@ -320,6 +322,8 @@ int muca_converge(muca_ctx *ctx, int n_sweeps, int max_iterations, int *n_iter_o
             conv = it;
             break;
         }
+        // intermediate thermalisation with the new weights before the next iteration
+        if (it < max_iterations && (rc = muca_thermalize(ctx, therm_sweeps))) return rc;
     }
     if (n_iter_out) *n_iter_out = conv;
     if (last) *last = st;

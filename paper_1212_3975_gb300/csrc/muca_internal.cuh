@@ -119,6 +119,8 @@ struct BatchJob {
     int flags;                  // staging of the sweep body: 4 table, 2 histogram, 1 lattice in smem
     int *active;                // 0: the lattice is frozen (converged) and every batch kernel skips it
     int *conv;                  // iteration at which the lattice converged, -1 before
+    uint32_t ctr3_therm;        // counter word 3 of thermalisation sweeps
+    uint32_t *therm;            // device counter of thermalisation sweeps (counter word 1)
 };
 
 }  // namespace muca

@@ -36,6 +36,20 @@ def test_converge_equals_oracle(muca, model, L, q, p, sweeps):
         assert g.iteration == n_o
 
 
+@pytest.mark.parametrize("model,L,q,p,sweeps,therm", [(POTTS, 4, 8, 5, 100, 7), (ISING, 8, 2, 8, 150, 13)])
+def test_converge_with_thermalization_equals_oracle(muca, model, L, q, p, sweeps, therm):
+    from oracle import MucaOracle
+    o = MucaOracle(model, L, q, p, 23)
+    n_o, _ = o.converge(sweeps, 300, therm)
+    with muca.Muca(model, L, q, p, 23) as g:
+        n_g, st = g.converge(sweeps, 300, therm)
+        assert n_g == n_o
+        assert n_g > 0 and st["flat"]
+        assert np.array_equal(g.get_lnw(), o.lnw)
+        E, M = g.get_energies()
+        assert np.array_equal(E, o.E) and np.array_equal(M, o.M)
+
+
 def test_converge_reports_no_convergence(muca):
     with muca.Muca(ISING, 4, 2, 1, 3) as g:
         n, st = g.converge(1, 2)
@@ -47,13 +61,14 @@ JOBS = [(ISING, 8, 2, 7, 31), (ISING, 16, 2, 40, 32), (POTTS, 8, 8, 33, 33), (IS
         (POTTS, 4, 8, 3, 35), (ISING, 4, 2, 1, 36)]
 
 
-def test_batch_converge_equals_standalone(muca):
+@pytest.mark.parametrize("therm", [0, 9])
+def test_batch_converge_equals_standalone(muca, therm):
     sweeps, max_it = 120, 60
     b = muca.MucaBatch(JOBS)
-    n_b = b.converge(sweeps, max_it)
+    n_b = b.converge(sweeps, max_it, therm)
     for j, (model, L, q, p, seed) in enumerate(JOBS):
         with muca.Muca(model, L, q, p, seed) as g:
-            n_s, _ = g.converge(sweeps, max_it)
+            n_s, _ = g.converge(sweeps, max_it, therm)
             assert n_b[j] == n_s, (JOBS[j], n_b[j], n_s)
             v = b.job(j)
             assert np.array_equal(v.get_lnw(), g.get_lnw()), JOBS[j]
@@ -65,7 +80,7 @@ def test_batch_converge_equals_standalone(muca):
     b.iterate(1, 10, graph=False)
     for j, (model, L, q, p, seed) in enumerate(JOBS):
         with muca.Muca(model, L, q, p, seed) as g:
-            g.converge(sweeps, max_it)
+            g.converge(sweeps, max_it, therm)
             H = g.iterate(10)
             g.update_weights()
             v = b.job(j)

@@ -113,6 +113,29 @@ def test_iterate_bit_exact_with_injected_table(muca, model, L, p, sweeps, cpb, s
     assert np.array_equal(M, o.M)
 
 
+@pytest.mark.parametrize("model,L,p", [(POTTS, 4, 9), (POTTS, 8, 33), (POTTS, 12, 40), (POTTS, 64, 35),
+                                       (ISING, 4, 5), (ISING, 32, 40), (ISING, 64, 33)])
+def test_thermalize_bit_exact_with_injected_table(muca, model, L, p):
+    """Thermalisation launches (no histogram, no records) against the oracle with the
+    same tables, including lattices of one word per row."""
+    q = 2 if model == ISING else 8
+    seed = 91
+    lnw = random_weights(model, L, 8, 0.42 if model == ISING else 1.3)
+    thr = weights.thresholds(model, L, lnw)
+    with muca.Muca(model, L, q, p, seed) as g:
+        g.set_lnw(lnw)
+        g.set_thresholds(thr)
+        g.thermalize(7)
+        g.thermalize(5)
+        spins = g.get_spins()
+        E, M = g.get_energies()
+    o = MucaOracle(model, L, q, p, seed)
+    o.thermalize(7, thr=thr)
+    o.thermalize(5, thr=thr)
+    assert np.array_equal(spins, o.spins)
+    assert np.array_equal(E, o.E) and np.array_equal(M, o.M)
+
+
 @pytest.mark.parametrize("model,L,p", [(ISING, 8, 37), (ISING, 64, 33), (POTTS, 6, 40),
                                        (POTTS, 32, 35)])
 def test_produce_records_and_samples(muca, model, L, p):

@@ -46,3 +46,17 @@ def test_converge_reports_no_convergence():
     n_iter, stats = o.converge(1, 2)   # one sweep per iteration cannot cover 15 bins
     assert n_iter == -1 and not stats["flat"]
     assert o.iteration == 2
+
+
+def test_intermediate_thermalization_runs_between_iterations():
+    # the thermalisation sweeps advance the thermalisation counter only after
+    # unconverged updates that are not the last allowed iteration
+    o = MucaOracle(ISING, 4, 2, 2, 5)
+    n_iter, _ = o.converge(1, 3, therm_sweeps=4)
+    assert n_iter == -1
+    from oracle.muca import PHASE_THERMALIZE
+    assert o.sweep_counter[PHASE_THERMALIZE] == 8
+    r = MucaOracle(ISING, 4, 2, 2, 5)
+    n_iter2, st = r.converge(60, 100, therm_sweeps=5)
+    assert n_iter2 > 0 and st["flat"]
+    assert r.sweep_counter[PHASE_THERMALIZE] == 5 * (n_iter2 - 1)
