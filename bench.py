@@ -268,6 +268,7 @@ def run_gpu(args):
         result["batched"] = batched_comparison(m, torch)
         result["other_workloads"] = other_workloads(m, torch, stream)
         result["statistical_study"] = statistical_study()
+        result["interface_tension"] = interface_tension()
     else:
         g.close()
     if rank == 0:
@@ -400,6 +401,25 @@ def statistical_study():
         "intermediate_thermalization": {"workload": "8-Potts 8x8, p = 16, M = Eq. 7 M_opt(8, 16) = %d, T sweeps "
                                                     "after every unconverged update, 16 seeds, <= 200 iterations" % M,
                                         **therm},
+        "seconds": round(time.perf_counter() - t0, 2),
+    }
+
+
+def interface_tension():
+    """sigma_od of the 8-state Potts model (Sec. 5), bounded: L = 8, 12, 16, four
+    independent runs of 16 chains each per L iterated to convergence together, 4000
+    production sweeps per converged run, equal-height analysis; sigma_inf from
+    sigma_od(L) = sigma_inf + c/L (small L: large finite-size corrections)."""
+    from paper_1212_3975_gb300 import study
+    t0 = time.perf_counter()
+    res, (s_inf, c) = study.sigma_od_scan([8, 12, 16])
+    fin = lambda x: None if not (isinstance(x, float) and math.isfinite(x)) else round(float(x), 6)  # noqa: E731
+    return {
+        "workload": "8-Potts L = 8, 12, 16, 4 runs x 16 chains, M = Eq. 7 M_opt(L, 16), <= 300 iterations, "
+                    "200 thermalisation + 4000 production sweeps per converged run, beta in [1.25, 1.45]",
+        "per_L": {str(L): {k: (fin(v) if isinstance(v, float) else v) for k, v in r.items()} for L, r in res.items()},
+        "sigma_inf_fit": fin(s_inf), "fit_c": fin(c),
+        "paper_sigma_inf": 0.045,
         "seconds": round(time.perf_counter() - t0, 2),
     }
 

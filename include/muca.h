@@ -271,6 +271,32 @@ muca_ctx *muca_batch_job(muca_batch *b, int j);
  * grid, staging (MUCA_STAGING_*) and launches per iteration. */
 int muca_batch_autotune(muca_batch *b, int n_sweeps, const char *cache_path, int chosen[3]);
 
+/* ---------------------------------------------------------------------------
+ * Order-disorder interface tension (Sec. 5)
+ * ------------------------------------------------------------------------- */
+
+/* Reweighted energy distribution of the production sums (Eq. 2 applied to the energy
+ * histogram): lnP_out[k][b] = ln n_b - ln W_b - beta_k E_b - ln sum_b'(...), FP64,
+ * -inf where the production run never visited bin b; W = the production weights.
+ * betas[n_beta] and lnP_out[n_beta][n_bins] may be host or device memory (caller-
+ * owned); the call allocates device scratch and synchronises.
+ * Errors: MUCA_ERR_ARG, MUCA_ERR_STATE (no production sums), MUCA_ERR_OOM, MUCA_ERR_CUDA. */
+int muca_energy_distribution(muca_ctx *ctx, const double *betas, int n_beta, double *lnP_out);
+
+/* sigma_od of Sec. 5 from the production sums: the inverse temperature beta_eqh at
+ * which the two peaks of ln P_beta (ordered, low energy; disordered, high energy) are
+ * equally high, and ln(P_max / P_min) there (mean peak height minus the minimum
+ * between them); sigma_od(L) = ln_ratio / (2 L).  Peaks at a beta: split the sampled
+ * bins at s (first: mid-range), highest bin on each side (first on ties), s moved to
+ * the lowest bin between them until it stays (<= 64 rounds); they count only with the
+ * dip strictly inside and below both.  beta_eqh: first interval of an n_grid-point
+ * uniform grid on [beta_lo, beta_hi] where ln P(low peak) - ln P(high peak) turns
+ * from negative to non-negative, then n_bisect bisection steps.  Outputs (host, may
+ * be NULL): *beta_eqh, *ln_ratio (NaN if no such beta), peaks[3] = (low peak, high
+ * peak, dip) bins (-1 if none).  Errors: as muca_energy_distribution. */
+int muca_interface_tension(muca_ctx *ctx, double beta_lo, double beta_hi, int n_grid, int n_bisect,
+                           double *beta_eqh, double *ln_ratio, int *peaks);
+
 /* Checkpoint / resume: the complete state (spins, E, M, Potts counts, ln W, the
  * recursion accumulator, thresholds, counters, seed, production sums) in one file.
  * Philox is counter-based, so a resumed run continues bit-identically. */

@@ -107,6 +107,21 @@ class Muca:
     def thermalize(self, n_sweeps):
         check(lib().muca_thermalize(self._h, n_sweeps))
 
+    def energy_distribution(self, betas):
+        """ln P_beta(E) of the production sums for every beta: [n_beta, n_bins] FP64."""
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        out = np.zeros((len(b), self.n_bins))
+        check(lib().muca_energy_distribution(self._h, _ptr(b), len(b), _ptr(out)))
+        return out
+
+    def interface_tension(self, beta_lo, beta_hi, n_grid=64, n_bisect=60):
+        """(beta_eqh, ln(P_max/P_min), (low peak, high peak, dip) bins, sigma_od(L)) of Sec. 5."""
+        be, lr = ctypes.c_double(), ctypes.c_double()
+        peaks = np.full(3, -1, dtype=np.int32)
+        check(lib().muca_interface_tension(self._h, beta_lo, beta_hi, n_grid, n_bisect, ctypes.byref(be),
+                                           ctypes.byref(lr), _ptr(peaks)))
+        return be.value, lr.value, tuple(int(x) for x in peaks), lr.value / (2.0 * self.L)
+
     def produce(self, n_sweeps, E_out="host", M_out="host"):
         """Production sweeps; returns (E, M) records [n_sweeps, p] (int32)."""
         if isinstance(E_out, str):

@@ -64,6 +64,10 @@ _SIGS = {
     "muca_iterate": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "muca_update_weights": (ctypes.c_int, [_P, ctypes.POINTER(MucaIterStats)]),
     "muca_thermalize": (ctypes.c_int, [_P, ctypes.c_int]),
+    "muca_energy_distribution": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "muca_interface_tension": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.c_void_p]),
     "muca_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(MucaIterStats)]),
     "muca_produce": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),

@@ -147,3 +147,54 @@ def speedup_runs(model, L, p_list, m1, seeds, max_iterations, seed0=7):
         n_iter[int(p)] = mean_n_iter(runs)
         per_chain[int(p)] = n_iter[int(p)] * M
     return n_iter, per_chain, statistical_speedup(per_chain) if 1 in per_chain else {}
+
+
+def fit_inverse_l(L_list, values):
+    """(v_inf, c) of v(L) = v_inf + c / L by linear least squares in 1/L."""
+    x = 1.0 / np.asarray(L_list, dtype=np.float64)
+    c, v_inf = np.polyfit(x, np.asarray(values, dtype=np.float64), 1)
+    return float(v_inf), float(c)
+
+
+def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, production=4000,
+                  beta_range=(1.25, 1.45), seed0=3):
+    """Order-disorder interface tension of the 8-state Potts model (Sec. 5) for every L:
+    `runs` independent MUCA runs of p chains each, iterated to convergence together
+    (muca_batch_converge at M = Eq. 7's M_opt(L, p)); every converged run is thermalised,
+    runs a production that keeps only the per-bin sums, and gives sigma_od(L) from the
+    equal-height analysis of muca_interface_tension.  sigma_od(L) is the mean over the
+    converged runs; finally sigma_od(L) = sigma_inf + c/L is fitted.
+
+    Returns ({L: dict(M, converged, N_iter, beta_eqh, sigma_od, sigma_err)},
+    (sigma_inf, c))."""
+    from . import check, lib
+    out = {}
+    for L in L_list:
+        M = max(10, int(round(eq7_m_opt(POTTS, L, p))))
+        jobs = [(POTTS, L, 8, p, seed0 + 100 * L + r) for r in range(runs)]
+        b = MucaBatch(jobs)
+        try:
+            n_iter = b.converge(M, max_iterations)
+            sig, bet = [], []
+            for j in range(runs):
+                if n_iter[j] < 0:
+                    continue
+                g = b.job(j)
+                g.thermalize(therm_sweeps)
+                check(lib().muca_produce(g.handle, production, None, None))
+                beta, ratio, peaks, sigma = g.interface_tension(*beta_range)
+                if math.isfinite(sigma):
+                    sig.append(sigma)
+                    bet.append(beta)
+        finally:
+            b.close()
+        conv = [int(x) for x in n_iter if x > 0]
+        out[int(L)] = {"M": M, "converged": "%d/%d" % (len(conv), runs),
+                       "N_iter": float(np.mean(conv)) if conv else math.nan,
+                       "beta_eqh": float(np.mean(bet)) if bet else math.nan,
+                       "sigma_od": float(np.mean(sig)) if sig else math.nan,
+                       "sigma_err": float(np.std(sig, ddof=1) / math.sqrt(len(sig))) if len(sig) > 1 else math.nan}
+    # the 1/L fit needs at least three sizes
+    Ls = [L for L in out if math.isfinite(out[L]["sigma_od"])]
+    fit = fit_inverse_l(Ls, [out[L]["sigma_od"] for L in Ls]) if len(Ls) >= 3 else (math.nan, math.nan)
+    return out, fit

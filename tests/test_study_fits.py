@@ -62,3 +62,9 @@ def test_speedup_from_scan():
     assert S[2] == pytest.approx(2.0, rel=1e-9)
     assert S[4] == pytest.approx(2.0, rel=1e-9)
     assert per_chain[4] == pytest.approx(study.m_opt_from_scan(*scan[4][::2])[1] / 4)
+
+
+def test_fit_inverse_l():
+    L = np.array([16, 24, 32, 48])
+    v_inf, c = study.fit_inverse_l(L, 0.045 + 0.3 / L)
+    assert v_inf == pytest.approx(0.045, abs=1e-12) and c == pytest.approx(0.3, abs=1e-10)
