@@ -66,11 +66,19 @@ extern "C" {
 #define MUCA_STAGING_SHARED 1 /* lattices copied into shared memory for a launch */
 #define MUCA_STAGING_GLOBAL 2 /* lattices stay in global memory (L2 / HBM) */
 
+/* ensembles: weights in the energy (multicanonical, Secs. 2-3) or, for the Ising
+ * model, in the magnetisation at a fixed inverse temperature (multimagnetic, Sec. 4
+ * and Fig. 6: the chain samples W(M) exp(-beta E); bins M = -V..V in steps of 2) */
+#define MUCA_ENSEMBLE_ENERGY 0
+#define MUCA_ENSEMBLE_MAGNETIZATION 1
+
 typedef struct muca_config {
     int recursion;        /* MUCA_RECURSION_*; default accumulated */
     int correction_width; /* bins for the boundary slope (Sec. 3); 0 -> L */
     int chains_per_block; /* multiple of 32, <= 256; 0 -> automatic */
     int staging;          /* MUCA_STAGING_*; 0 -> automatic */
+    int ensemble;         /* MUCA_ENSEMBLE_*; 0 -> energy */
+    double beta;          /* inverse temperature of the multimagnetic ensemble */
 } muca_config;
 
 /* Convergence statistics of one merged histogram over the accessible bins (Sec. 3:
@@ -95,6 +103,11 @@ uint64_t muca_kernel_launches(void);
 
 /* Create p chains of the given model on an L x L periodic lattice (Sec. 3) and start
  * them at infinite temperature: i.i.d. uniform spins, ln W = 0 (Sec. 3).
+ * With cfg->ensemble = MUCA_ENSEMBLE_MAGNETIZATION (Ising only) the weights, the
+ * histograms and the convergence test are over the V+1 magnetisation bins
+ * (M + V)/2 and the acceptance includes exp(-cfg->beta dE); production then records
+ * (E, M) per sweep but keeps no energy sums, so the reweighting and interface-tension
+ * calls return MUCA_ERR_STATE, and batches reject such contexts.
  *  model: MUCA_ISING (q must be 2, L even, 4 <= L <= 1024) or MUCA_POTTS (q must
  *         be 8, 3 <= L <= 255); p: 1 <= p <= 2^24 chains; seed: seed >> 32 < 2^30.
  *  cfg:   NULL for defaults; cuda_stream: a cudaStream_t, NULL = legacy default.

@@ -19,13 +19,19 @@ PHASE_INIT, PHASE_ITERATE, PHASE_THERMALIZE, PHASE_PRODUCE = 0, 1, 2, 3
 
 class MucaOracle:
     def __init__(self, model, L, q, p, seed, chains=None, accumulated=True,
-                 correction_width=None):
+                 correction_width=None, muma_beta=None):
+        """muma_beta: the multimagnetic Ising ensemble (weights in M at this beta,
+        Sec. 4 / Fig. 6) instead of weights in E."""
         if model == weights.ISING:
             q = 2
         self.model, self.L, self.q, self.p, self.seed = model, L, q, p, seed
+        self.muma_beta = muma_beta
         self.V = L * L
         self.n_bins = weights.n_bins(model, L)
         self.acc = weights.accessible(model, L)
+        if muma_beta is not None:
+            assert model == weights.ISING
+            self.acc = np.ones(self.n_bins, dtype=bool)  # every M = -V..V step 2
         self.accumulated = accumulated
         self.correction_width = L if correction_width is None else correction_width
         if chains is None:
@@ -44,13 +50,23 @@ class MucaOracle:
         self.P = np.zeros(self.n_bins)
         self.iteration = 0
         self.sweep_counter = {PHASE_THERMALIZE: 0, PHASE_PRODUCE: 0}
-        self.thr = weights.thresholds(model, L, self.lnw, self.acc)
+        self.thr = self._thresholds(self.lnw)
+
+    def _thresholds(self, lnw):
+        if self.muma_beta is not None:
+            return weights.thresholds_muma(self.L, lnw, self.muma_beta)
+        return weights.thresholds(self.model, self.L, lnw, self.acc)
 
     def _contiguous(self):
         ids = self.chain_ids
         return ids == list(range(ids[0], ids[0] + len(ids)))
 
     def _run(self, phase, iteration, sweep0, n_sweeps, thr, hist, record):
+        if self.muma_beta is not None:
+            assert self._contiguous()
+            H, er, mr = sampler.run_muma_sweeps(self.L, self.seed, phase, iteration, sweep0, n_sweeps,
+                                                self.chain_ids[0], self.spins, self.E, self.M, thr, record)
+            return (H if hist else None), [], er, mr
         if self._contiguous():
             # one call over all chains (run in parallel on the host cores)
             h, er, mr = sampler.run_sweeps(self.model, self.L, self.q, self.seed, phase,
@@ -103,7 +119,7 @@ class MucaOracle:
                                                  accumulated=self.accumulated,
                                                  correction_width=self.correction_width,
                                                  acc=self.acc)
-        self.thr = weights.thresholds(self.model, self.L, self.lnw, self.acc)
+        self.thr = self._thresholds(self.lnw)
         return stats
 
     def converge(self, n_sweeps, max_iterations, therm_sweeps=0):
@@ -125,7 +141,7 @@ class MucaOracle:
 
     def set_lnw(self, lnw):
         self.lnw = np.asarray(lnw, dtype=np.float64).copy()
-        self.thr = weights.thresholds(self.model, self.L, self.lnw, self.acc)
+        self.thr = self._thresholds(self.lnw)
 
     def thermalize(self, n_sweeps, thr=None):
         thr = self.thr if thr is None else thr

@@ -287,6 +287,74 @@ int orc_sweeps(int model, int L, int q, uint64_t seed, int phase, uint32_t itera
     return status ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Multimagnetic Ising (Sec. 4, Fig. 6): weights in the magnetisation M at a    */
+/* fixed inverse temperature beta, i.e. the chain samples W(M) exp(-beta E).    */
+/* Readings: bin of M = (M + V) / 2 (all V + 1 bins reachable); the threshold   */
+/* table has 10 columns per bin, column 5 * (s == +1) + n for the flipped spin  */
+/* s and its n unequal neighbours (0..4), so that E' - E = 8 - 4n and the bin    */
+/* moves to (M - 2s + V) / 2; the random streams, the sweep order and the        */
+/* acceptance test are those of the Ising chain above; after every attempt the   */
+/* chain histogram at the current M bin is incremented.                          */
+/* ------------------------------------------------------------------------- */
+static int run_muma_chain(int L, uint64_t seed, uint32_t phase, uint32_t iteration, uint32_t sweep0,
+                          int n_sweeps, int64_t chain, int8_t *s, int64_t *E_io, int64_t *M_io,
+                          const uint32_t *thr, uint64_t *H, int32_t *E_rec, int32_t *M_rec,
+                          int64_t rec_stride)
+{
+    int V = L * L;
+    int64_t E = *E_io, M = *M_io;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        uint32_t sweep = sweep0 + (uint32_t)sw;
+        for (int i = 0; i < V; ++i) {
+            int x = i % L, y = i / L;
+            int nb[4];
+            nb[0] = site_of(L, (x + 1) % L, y);
+            nb[1] = site_of(L, (x + L - 1) % L, y);
+            nb[2] = site_of(L, x, (y + 1) % L);
+            nb[3] = site_of(L, x, (y + L - 1) % L);
+            uint32_t w[4];
+            draw_block(seed, chain, (uint32_t)(i >> 2), sweep, iteration, phase, w);
+            uint32_t u = w[i & 3];
+            int old = s[i];
+            int unequal = 0;
+            for (int k = 0; k < 4; ++k) unequal += (s[nb[k]] != old);
+            int64_t b = (M + V) / 2;
+            uint32_t A = thr[b * 10 + 5 * (old == 1) + unequal];
+            if ((A == 0xFFFFFFFFu) || (u < A)) {
+                s[i] = (int8_t)(-old);
+                E += 8 - 4 * unequal;
+                M -= 2 * old;
+            }
+            if (H) H[(M + V) / 2] += 1;
+        }
+        if (orc_energy(ORC_ISING, L, s) != E) return -1;
+        if (orc_magnetization(ORC_ISING, L, 2, s) != M) return -1;
+        if (E_rec) E_rec[(int64_t)sw * rec_stride] = (int32_t)E;
+        if (M_rec) M_rec[(int64_t)sw * rec_stride] = (int32_t)M;
+    }
+    *E_io = E;
+    *M_io = M;
+    return 0;
+}
+
+/* As orc_sweeps for the multimagnetic Ising chain; thr: [V + 1][10]; H: [n_chains][V + 1]. */
+int orc_muma_sweeps(int L, uint64_t seed, int phase, uint32_t iteration, uint32_t sweep0, int n_sweeps,
+                    int64_t chain0, int n_chains, int8_t *spins, int64_t *E, int64_t *M, const uint32_t *thr,
+                    uint64_t *H, int32_t *E_rec, int32_t *M_rec)
+{
+    int V = L * L;
+    int status = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(|:status)
+    for (int c = 0; c < n_chains; ++c) {
+        status |= run_muma_chain(L, seed, (uint32_t)phase, iteration, sweep0, n_sweeps, chain0 + c,
+                                 spins + (int64_t)c * V, &E[c], &M[c], thr,
+                                 H ? H + (int64_t)c * (V + 1) : NULL,
+                                 E_rec ? E_rec + c : NULL, M_rec ? M_rec + c : NULL, (int64_t)n_chains);
+    }
+    return status ? -1 : 0;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -36,6 +36,11 @@ def lib():
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]
         L.orc_sweeps.restype = ctypes.c_int
+        L.orc_muma_sweeps.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32,
+                                      ctypes.c_uint32, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_muma_sweeps.restype = ctypes.c_int
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = ctypes.c_int
         _lib = L
@@ -112,3 +117,25 @@ def run_sweeps(model, L, q, seed, phase, iteration, sweep0, n_sweeps, chain0,
 
 def max_threads():
     return int(lib().orc_max_threads())
+
+
+def run_muma_sweeps(L, seed, phase, iteration, sweep0, n_sweeps, chain0, spins, E, M, thr,
+                    record=False):
+    """Multimagnetic Ising sweeps (weights in M at a fixed beta, folded into thr
+    [V + 1, 10]); returns (merged M histogram [V + 1] uint64, E_rec, M_rec)."""
+    n_chains = spins.shape[0]
+    nb = L * L + 1
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    assert thr.shape == (nb, 10)
+    H = np.zeros((n_chains, nb), dtype=np.uint64)
+    E_rec = np.zeros((n_sweeps, n_chains), dtype=np.int32) if record else None
+    M_rec = np.zeros((n_sweeps, n_chains), dtype=np.int32) if record else None
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous
+    rc = lib().orc_muma_sweeps(L, seed, phase, iteration, sweep0, n_sweeps, chain0, n_chains, _ptr(spins),
+                               _ptr(E), _ptr(M), _ptr(thr), _ptr(H), _ptr(E_rec), _ptr(M_rec))
+    if rc != 0:
+        raise RuntimeError("oracle invariant failed: running E/M != recomputed")
+    merged = np.zeros(nb, dtype=np.uint64)
+    for c in range(n_chains):
+        merged += H[c]
+    return merged, E_rec, M_rec

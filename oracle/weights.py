@@ -95,6 +95,30 @@ def thresholds(model, L, lnw, acc=None):
     return out
 
 
+def thresholds_muma(L, lnw, beta):
+    """Thresholds of the multimagnetic Ising chain (weights W(M) at inverse temperature
+    beta): for M bin b = (M + V)/2 and column 5 (s == +1) + n, with n unequal
+    neighbours of the flipped spin s: b' = b - s, dE = 8 - 4n,
+    d = (lnW[b'] - lnW[b]) - beta dE in FP64; A as in `thresholds`; 0 for b' outside
+    the range."""
+    nb = L * L + 1
+    out = np.zeros((nb, 10), dtype=np.uint32)
+    for b in range(nb):
+        for col in range(10):
+            s = 1 if col >= 5 else -1
+            n = col - 5 if col >= 5 else col
+            bp = b - s
+            if bp < 0 or bp >= nb:
+                continue
+            d = (float(lnw[bp]) - float(lnw[b])) - beta * float(8 - 4 * n)
+            if d >= 0.0:
+                A = ALWAYS
+            else:
+                A = min(math.floor(math.ldexp(math.exp(d), 32)), ALWAYS)
+            out[b, col] = A
+    return out
+
+
 def iteration_stats(model, L, H, acc=None):
     """Convergence statistics of one merged histogram (Sec. 3), over accessible bins.
 

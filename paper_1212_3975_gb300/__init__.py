@@ -10,8 +10,9 @@ import ctypes
 import numpy as np
 
 from ._muca import (  # noqa: F401
-    MUCA_BF16, MUCA_FP32, MUCA_FP64, MUCA_ISING, MUCA_POTTS, MUCA_RECURSION_ACCUMULATED,
-    MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL, MUCA_STAGING_SHARED,
+    MUCA_BF16, MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION, MUCA_FP32, MUCA_FP64, MUCA_ISING,
+    MUCA_POTTS, MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL,
+    MUCA_STAGING_SHARED,
     MucaConfig, MucaError, MucaIterStats, MucaJob, check, declared_symbols, lib)
 
 PRECISIONS = {"fp64": MUCA_FP64, "fp32": MUCA_FP32, "bf16": MUCA_BF16}
@@ -40,12 +41,16 @@ class Muca:
 
     def __init__(self, model, L, q, p, seed, recursion=MUCA_RECURSION_ACCUMULATED,
                  correction_width=0, chains_per_block=0, staging=MUCA_STAGING_AUTO,
-                 stream=None, _handle=None):
+                 stream=None, _handle=None, muma_beta=None):
+        """muma_beta: multimagnetic Ising ensemble (weights in M at this inverse
+        temperature) instead of the multicanonical one."""
         self._h = ctypes.c_void_p()
         if _handle is not None:
             self._h = _handle
         else:
-            cfg = MucaConfig(recursion, correction_width, chains_per_block, staging)
+            ens = MUCA_ENSEMBLE_ENERGY if muma_beta is None else MUCA_ENSEMBLE_MAGNETIZATION
+            cfg = MucaConfig(recursion, correction_width, chains_per_block, staging, ens,
+                             0.0 if muma_beta is None else float(muma_beta))
             check(lib().muca_init(ctypes.byref(self._h), model, L, q, p, seed,
                                   ctypes.byref(cfg), _ptr(stream)))
         self.model, self.L, self.q, self.p = model, L, q, p
@@ -223,7 +228,7 @@ class MucaBatch:
     def __init__(self, jobs, recursion=MUCA_RECURSION_ACCUMULATED, correction_width=0,
                  staging=MUCA_STAGING_AUTO, stream=None):
         arr = (MucaJob * len(jobs))(*[MucaJob(m, L, q, p, seed) for (m, L, q, p, seed) in jobs])
-        cfg = MucaConfig(recursion, correction_width, 0, staging)
+        cfg = MucaConfig(recursion, correction_width, 0, staging, MUCA_ENSEMBLE_ENERGY, 0.0)
         self._h = ctypes.c_void_p()
         check(lib().muca_batch_create(ctypes.byref(self._h), arr, len(jobs), ctypes.byref(cfg),
                                       _ptr(stream)))

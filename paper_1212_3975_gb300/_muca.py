@@ -17,6 +17,7 @@ MUCA_ERR_TIMEOUT, MUCA_ERR_STATE, MUCA_ERR_IO = -4, -5, -6
 MUCA_FP64, MUCA_FP32, MUCA_BF16 = 0, 1, 2
 MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE = 0, 1
 MUCA_STAGING_AUTO, MUCA_STAGING_SHARED, MUCA_STAGING_GLOBAL = 0, 1, 2
+MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION = 0, 1
 
 ERROR_NAMES = {-1: "MUCA_ERR_ARG", -2: "MUCA_ERR_CUDA", -3: "MUCA_ERR_OOM",
                -4: "MUCA_ERR_TIMEOUT", -5: "MUCA_ERR_STATE", -6: "MUCA_ERR_IO"}
@@ -24,7 +25,8 @@ ERROR_NAMES = {-1: "MUCA_ERR_ARG", -2: "MUCA_ERR_CUDA", -3: "MUCA_ERR_OOM",
 
 class MucaConfig(ctypes.Structure):
     _fields_ = [("recursion", ctypes.c_int), ("correction_width", ctypes.c_int),
-                ("chains_per_block", ctypes.c_int), ("staging", ctypes.c_int)]
+                ("chains_per_block", ctypes.c_int), ("staging", ctypes.c_int),
+                ("ensemble", ctypes.c_int), ("beta", ctypes.c_double)]
 
 
 class MucaIterStats(ctypes.Structure):

@@ -224,6 +224,8 @@ int configure(muca_batch *b)
     for (int i = 0; i < b->n_jobs; ++i) {
         muca_ctx *c = b->ctx[i];
         c->cfg.staging = b->staging;
+        if (c->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
+            return fail(MUCA_ERR_ARG, "batched lattices need the energy ensemble (job " + std::to_string(i) + ")");
         const SweepPlan pl = plan_sweeps(c);
         if (!pl.warp_specialized)
             return fail(MUCA_ERR_ARG, "batched lattices need L % 4 == 0 (job " + std::to_string(i) + ")");

@@ -111,6 +111,8 @@ extern "C" int muca_energy_distribution(muca_ctx *ctx, const double *betas, int 
 {
     if (!ctx) return fail(MUCA_ERR_ARG, "null context");
     if (!betas || !lnP_out || n_beta < 1) return fail(MUCA_ERR_ARG, "need betas, lnP_out and n_beta >= 1");
+    if (ctx->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
+        return fail(MUCA_ERR_STATE, "no energy production sums in the multimagnetic ensemble");
     if (!ctx->samples_active) return fail(MUCA_ERR_STATE, "no production sums: run muca_produce first");
     cudaSetDevice(ctx->device);
     double *d_b = nullptr, *d_o = nullptr;

@@ -186,7 +186,7 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
         cudaGetLastError();
         return fail(MUCA_ERR_CUDA, "no CUDA device available");
     }
-    muca_config c0{MUCA_RECURSION_ACCUMULATED, 0, 0, MUCA_STAGING_AUTO};
+    muca_config c0{MUCA_RECURSION_ACCUMULATED, 0, 0, MUCA_STAGING_AUTO, MUCA_ENSEMBLE_ENERGY, 0.0};
     if (cfg) {
         c0 = *cfg;
         if (c0.recursion != MUCA_RECURSION_ACCUMULATED && c0.recursion != MUCA_RECURSION_SIMPLE)
@@ -195,6 +195,10 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
         if (c0.chains_per_block < 0 || c0.chains_per_block > 256 || (c0.chains_per_block % 32))
             return fail(MUCA_ERR_ARG, "chains_per_block must be 0 or a multiple of 32 up to 256");
         if (c0.staging < 0 || c0.staging > 2) return fail(MUCA_ERR_ARG, "unknown staging");
+        if (c0.ensemble != MUCA_ENSEMBLE_ENERGY && c0.ensemble != MUCA_ENSEMBLE_MAGNETIZATION)
+            return fail(MUCA_ERR_ARG, "unknown ensemble");
+        if (c0.ensemble == MUCA_ENSEMBLE_MAGNETIZATION && (model != MUCA_ISING || !std::isfinite(c0.beta)))
+            return fail(MUCA_ERR_ARG, "the multimagnetic ensemble needs the Ising model and a finite beta");
     }
     muca_ctx *c = new muca_ctx();
     std::memset(static_cast<void *>(c), 0, sizeof(muca_ctx));
@@ -204,7 +208,7 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
     c->p = p;
     c->V = L * L;
     c->n_bins = n_bins_of(model, L);
-    c->n_de = n_de_of(model);
+    c->n_de = c0.ensemble == MUCA_ENSEMBLE_MAGNETIZATION ? 10 : n_de_of(model);
     c->seed = seed;
     c->cfg = c0;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -218,6 +222,7 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
         return rc;
     }
     std::vector<uint8_t> acc = accessible_bins(model, L);
+    if (c0.ensemble == MUCA_ENSEMBLE_MAGNETIZATION) acc.assign(c->n_bins, 1);  // every M = -V..V step 2
     cudaError_t e;
     if ((e = cudaMemcpyAsync(c->d_acc, acc.data(), acc.size(), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->d_lnw, 0, sizeof(double) * c->n_bins, c->stream)) != cudaSuccess ||
@@ -399,6 +404,8 @@ int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
 {
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
+    if (ctx->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
+        return fail(MUCA_ERR_STATE, "no energy production sums in the multimagnetic ensemble");
     if (!betas || n_beta < 1) return fail(MUCA_ERR_ARG, "need at least one beta");
     if (precision != MUCA_FP64 && precision != MUCA_FP32 && precision != MUCA_BF16)
         return fail(MUCA_ERR_ARG, "unknown precision");
@@ -554,7 +561,7 @@ int muca_save(muca_ctx *ctx, const char *path)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "MUCACKP1", 8);
-    h.version = 1;
+    h.version = 2;
     h.model = ctx->model;
     h.L = ctx->L;
     h.q = ctx->q;
@@ -593,7 +600,7 @@ int muca_load(muca_ctx **out, const char *path, void *cuda_stream)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(MUCA_ERR_IO, std::string("cannot open ") + path);
     CkptHeader h;
-    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "MUCACKP1", 8) != 0 || h.version != 1) {
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "MUCACKP1", 8) != 0 || h.version != 2) {
         std::fclose(f);
         return fail(MUCA_ERR_IO, "not a checkpoint file (bad header)");
     }

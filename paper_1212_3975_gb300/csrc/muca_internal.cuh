@@ -191,6 +191,10 @@ SweepPlan plan_sweeps(const muca_ctx *ctx);
 cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st);
 int launch_ktab(muca_ctx *ctx);
 size_t ws_extra_smem(int model);
+// multimagnetic Ising ensemble (muma.cu)
+int launch_muma_thresholds(muca_ctx *ctx);
+int launch_muma_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,
+                       int32_t *E_rec, int32_t *M_rec);
 cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,
                             cudaStream_t st);
 cudaError_t launch_fast_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist,

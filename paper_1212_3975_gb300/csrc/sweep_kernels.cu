@@ -474,6 +474,8 @@ SweepPlan plan_sweeps(const muca_ctx *ctx)
 int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,
                   int32_t *E_rec, int32_t *M_rec, bool samples)
 {
+    if (ctx->cfg.ensemble == MUCA_ENSEMBLE_MAGNETIZATION)
+        return launch_muma_sweeps(ctx, phase, n_sweeps, sweep0, iteration, hist, E_rec, M_rec);
     SweepPlan pl = plan_sweeps(ctx);
     const bool fast = (ctx->L % 4) == 0;
     if (fast && ctx->ktab_dirty) {

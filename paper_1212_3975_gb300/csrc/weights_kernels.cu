@@ -258,6 +258,7 @@ cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr,
 
 int launch_thresholds(muca_ctx *ctx)
 {
+    if (ctx->cfg.ensemble == MUCA_ENSEMBLE_MAGNETIZATION) return launch_muma_thresholds(ctx);
     const int n = ctx->n_bins * ctx->n_de;
     thresholds_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_lnw, ctx->d_acc, ctx->d_thr, ctx->model,
                                                                ctx->n_bins, ctx->n_de);
