@@ -392,12 +392,31 @@ def statistical_study():
             "converged": "%d/%d" % (len(ok), len(runs)),
             "median_n_iter": fin(float(np.median(ok))) if len(ok) else None,
             "median_sweeps_per_chain": fin(float(np.median(ok * M + (ok - 1) * T))) if len(ok) else None}
+    # multimagnetic Ising at beta = (3/2) beta_0 (Sec. 4, Fig. 6): the same scan, with
+    # the weights in M; one context per run
+    beta_mm = 1.5 * math.log(1.0 + math.sqrt(2.0)) / 2.0
+    # (a single chain rarely converges within the cap here, so the speedup is quoted
+    # relative to p = 4: S*_p / S*_4 = [N_iter M]_4 / [N_iter M]_p)
+    ps_mm = [4, 16, 64]
+    scan_mm = study.m_scan(study.ISING, 8, ps_mm, [0.5, 1.0, 2.0, 4.0], 3, 200,
+                           M_center=lambda p: 1000.0 / p, muma_beta=beta_mm)
+    m_mm, per_chain_mm, _ = study.speedup_from_scan(scan_mm)
+    muma = {
+        "workload": "multimagnetic 8x8 Ising at beta = (3/2) beta_0, p in {4, 16, 64}, 3 seeds per (p, M), "
+                    "M grid x{0.5..4} around 1000/p, <= 200 iterations",
+        "M_opt": {str(p): fin(m_mm[p]) for p in ps_mm},
+        "sweeps_per_chain_to_convergence": {str(p): fin(per_chain_mm[p]) for p in ps_mm},
+        "S_star_relative_to_p4": {str(p): fin(per_chain_mm[4] / per_chain_mm[p])
+                                  if math.isfinite(per_chain_mm[p]) and math.isfinite(per_chain_mm[4]) else None
+                                  for p in ps_mm},
+    }
     return {
         "workload": "8x8 Ising, p in 1..32, 10 seeds per (p, M), M grid x{0.5..4} around Eq. 7, <= 400 iterations",
         "M_opt": {str(p): fin(m_opt[p]) for p in ps},
         "M1_fit": round(m1, 1), "M1_eq7": round(study.eq7_m_opt(study.ISING, 8, 1), 1),
         "sweeps_per_chain_to_convergence": {str(p): fin(per_chain[p]) for p in ps},
         "S_star": {str(p): fin(S[p]) for p in ps},
+        "multimagnetic": muma,
         "intermediate_thermalization": {"workload": "8-Potts 8x8, p = 16, M = Eq. 7 M_opt(8, 16) = %d, T sweeps "
                                                     "after every unconverged update, 16 seeds, <= 200 iterations" % M,
                                         **therm},

@@ -33,14 +33,23 @@ def eq7_m_opt(model, L, p):
     return a * L ** (2.0 + b) / p
 
 
-def n_iter_runs(model, L, p_list, M, seeds, max_iterations, seed0=1, therm_sweeps=0):
+def n_iter_runs(model, L, p_list, M, seeds, max_iterations, seed0=1, therm_sweeps=0, muma_beta=None):
     """N_iter of every (p, seed) at M sweeps per iteration and chain, from one batch
-    (therm_sweeps: intermediate thermalisation after every unconverged update).
+    (therm_sweeps: intermediate thermalisation after every unconverged update).  With
+    muma_beta the runs are multimagnetic Ising runs (weights in M at that beta), one
+    context after another (batches hold the energy ensemble only).
 
     Returns {p: array of N_iter over the seeds} (-1 where a run did not converge
     within max_iterations)."""
     q = 2 if model == ISING else 8
     jobs = [(model, L, q, int(p), seed0 + 1000 * i + s) for i, p in enumerate(p_list) for s in range(seeds)]
+    if muma_beta is not None:
+        from . import Muca
+        n = np.full(len(jobs), -1, dtype=np.int32)
+        for k, (m, LL, qq, pp, sd) in enumerate(jobs):
+            with Muca(m, LL, qq, pp, sd, muma_beta=muma_beta) as g:
+                n[k] = g.converge(int(M), max_iterations, therm_sweeps)[0]
+        return {int(p): n[i * seeds:(i + 1) * seeds].copy() for i, p in enumerate(p_list)}
     b = MucaBatch(jobs)
     try:
         n = b.converge(int(M), max_iterations, therm_sweeps)
@@ -101,7 +110,8 @@ def statistical_speedup(sweeps_per_chain):
     return {p: base / v for p, v in sweeps_per_chain.items()}
 
 
-def m_scan(model, L, p_list, M_factors, seeds, max_iterations, M_center=None, seed0=1, therm_sweeps=0):
+def m_scan(model, L, p_list, M_factors, seeds, max_iterations, M_center=None, seed0=1, therm_sweeps=0,
+           muma_beta=None):
     """N_iter over a grid of M for every p.  The grid is geometric around M_center(p)
     (default: Eq. 7's M_opt(L, p)); runs sharing an M share one batch.
 
@@ -115,7 +125,7 @@ def m_scan(model, L, p_list, M_factors, seeds, max_iterations, M_center=None, se
             by_M.setdefault(M, []).append(p)
     res = {p: {} for p in grid}
     for M, ps in sorted(by_M.items()):
-        runs = n_iter_runs(model, L, ps, M, seeds, max_iterations, seed0, therm_sweeps)
+        runs = n_iter_runs(model, L, ps, M, seeds, max_iterations, seed0, therm_sweeps, muma_beta)
         for p in ps:
             res[p][M] = mean_n_iter(runs[p])
     out = {}
