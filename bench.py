@@ -237,6 +237,18 @@ def run_gpu(args):
                      "max clock" % sm_max,
         "occupied_schedulers": occupied,
         "frac_of_occupied_schedulers": achieved / (peak * occupied / 608.0),
+        # the three bounds on attempts/ns of the sweeps (all at the measured max clock):
+        # issue (every scheduler busy at this instruction count), shared-memory LSU (one
+        # wavefront per clock per SM at this wavefront count) and chain latency (p chains,
+        # each at the cycles per attempt of the decider's site loop measured alone on
+        # one warp)
+        "bounds_attempts_per_ns": {
+            "issue": 152 * 4 * sm_max * 1e6 / inst_per_attempt / 1e9,
+            "lsu": 152 * sm_max * 1e6 / SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 / 1e9,
+            "latency": w["p"] * sm_max * 1e6 / DECIDER_CYCLES_PER_ATTEMPT_ALONE / 1e9,
+        },
+        "frac_of_latency_bound": (att_per_launch / (sweep_avg_ms * 1e6))
+        / (w["p"] * sm_max * 1e6 / DECIDER_CYCLES_PER_ATTEMPT_ALONE / 1e9),
     }
     result = {
         "metric": METRIC, "value": value, "unit": "attempts/ns", "n_gpus": world,
@@ -488,6 +500,11 @@ INST_PER_ATTEMPT_ISING_L64 = 2.07
 # dram__bytes_read.sum + dram__bytes_write.sum of one weight-iteration launch of the same
 # kernel (staging of table, histogram and lattices only; independent of the sweep count)
 TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = 685568
+# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / attempts of the same capture
+SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 = 0.38
+# cycles per site of the decider's 32-site loop run alone on one warp (a replica of the
+# loop with the same table, draws and dependency structure, clock64-timed on a GB300)
+DECIDER_CYCLES_PER_ATTEMPT_ALONE = 43.1
 
 
 def run_probe(args):
