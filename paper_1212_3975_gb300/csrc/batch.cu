@@ -226,7 +226,7 @@ int configure(muca_batch *b)
         c->cfg.staging = b->staging;
         if (c->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
             return fail(MUCA_ERR_ARG, "batched lattices need the energy ensemble (job " + std::to_string(i) + ")");
-        const SweepPlan pl = plan_sweeps(c);
+        const SweepPlan pl = plan_sweeps(c, false);  // the batched kernel counts per attempt
         if (!pl.warp_specialized)
             return fail(MUCA_ERR_ARG, "batched lattices need L % 4 == 0 (job " + std::to_string(i) + ")");
         BatchJob &j = b->h_jobs[i];

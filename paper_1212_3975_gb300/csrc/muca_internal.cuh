@@ -97,6 +97,7 @@ struct SweepArgs {
 // staging flags of a sweep launch
 struct SweepPlan {
     bool table_smem, hist_smem, lattice_smem;
+    bool hist_pairs;        // Ising warp-specialised: shared histogram of attempt pairs
     bool warp_specialized;  // decider / producer / bookkeeper warps per 32 chains
     int chains_per_block;
     size_t smem_bytes;
@@ -187,7 +188,7 @@ int launch_update(muca_ctx *ctx);
 int launch_stats(muca_ctx *ctx);
 int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision,
                     double *d_out /* [4][n_beta] */);
-SweepPlan plan_sweeps(const muca_ctx *ctx);
+SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs = true);
 cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st);
 int launch_ktab(muca_ctx *ctx);
 size_t ws_extra_smem(int model);

@@ -437,7 +437,7 @@ cudaError_t dispatch_mode(const SweepArgs &a, const SweepPlan &pl, int blocks, b
 
 }  // namespace
 
-SweepPlan plan_sweeps(const muca_ctx *ctx)
+SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs)
 {
     SweepPlan pl;
     int cpb = ctx->cfg.chains_per_block;
@@ -467,6 +467,12 @@ SweepPlan plan_sweeps(const muca_ctx *ctx)
     const int staging = ctx->cfg.staging;
     pl.lattice_smem = staging == MUCA_STAGING_SHARED || (staging == MUCA_STAGING_AUTO && used + lat <= cap);
     if (pl.lattice_smem) used += lat;
+    // Ising warp-specialised launches: the histogram of attempt pairs (5 counts per
+    // bin) when it fits beside the table and the lattices
+    const size_t pairs = ((size_t)ctx->n_bins * 5 * 4 + 15) & ~(size_t)15;
+    pl.hist_pairs = allow_pairs && ws && ctx->model == MUCA_ISING && pl.table_smem && pl.hist_smem &&
+                    pl.lattice_smem && used - hist + pairs <= cap;
+    if (pl.hist_pairs) used += pairs - hist;
     pl.smem_bytes = used;
     return pl;
 }

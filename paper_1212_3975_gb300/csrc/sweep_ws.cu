@@ -5,11 +5,11 @@ namespace muca {
 namespace {
 using namespace ws;
 
-template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
 __global__ void __launch_bounds__(128) ising_ws_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    ising_ws_body<HIST, RECORD, TSMEM, HSMEM, LSMEM>(a, blockIdx.x, smem);
+    ising_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM>(a, blockIdx.x, smem);
 }
 
 // iteration and production launches: five warps (decider, 3 producers, bookkeeper)
@@ -20,11 +20,13 @@ __global__ void __launch_bounds__(160) potts_ws_kernel(SweepArgs a)
     potts_ws_body<HIST, RECORD, TSMEM, HSMEM, LSMEM, true>(a, blockIdx.x, smem);
 }
 
-template <int MODEL, bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+// HMODE: histogram in global memory (0), shared per attempt (1), shared per pair of
+// attempts (2, Ising only)
+template <int MODEL, bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
 cudaError_t launch_ws(const SweepArgs &a, int blocks, size_t smem, cudaStream_t st)
 {
-    auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HSMEM, LSMEM>
-                                    : potts_ws_kernel<HIST, RECORD, TSMEM, HSMEM, LSMEM>;
+    auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM>
+                                    : potts_ws_kernel<HIST, RECORD, TSMEM, HMODE != 0, LSMEM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -36,16 +38,19 @@ cudaError_t launch_ws(const SweepArgs &a, int blocks, size_t smem, cudaStream_t 
 template <int MODEL, bool HIST, bool RECORD>
 cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size_t smem, cudaStream_t st)
 {
+    // pair histogram: planned only with the table and the lattices in shared memory
+    if (MODEL == MUCA_ISING && HIST && pl.hist_smem && pl.hist_pairs)
+        return launch_ws<MODEL, HIST, RECORD, true, 2, true>(a, blocks, smem, st);
     const int key = (pl.table_smem ? 4 : 0) | ((HIST && pl.hist_smem) ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
     switch (key) {
-    case 0: return launch_ws<MODEL, HIST, RECORD, false, false, false>(a, blocks, smem, st);
-    case 1: return launch_ws<MODEL, HIST, RECORD, false, false, true>(a, blocks, smem, st);
-    case 2: return launch_ws<MODEL, HIST, RECORD, false, true, false>(a, blocks, smem, st);
-    case 3: return launch_ws<MODEL, HIST, RECORD, false, true, true>(a, blocks, smem, st);
-    case 4: return launch_ws<MODEL, HIST, RECORD, true, false, false>(a, blocks, smem, st);
-    case 5: return launch_ws<MODEL, HIST, RECORD, true, false, true>(a, blocks, smem, st);
-    case 6: return launch_ws<MODEL, HIST, RECORD, true, true, false>(a, blocks, smem, st);
-    default: return launch_ws<MODEL, HIST, RECORD, true, true, true>(a, blocks, smem, st);
+    case 0: return launch_ws<MODEL, HIST, RECORD, false, 0, false>(a, blocks, smem, st);
+    case 1: return launch_ws<MODEL, HIST, RECORD, false, 0, true>(a, blocks, smem, st);
+    case 2: return launch_ws<MODEL, HIST, RECORD, false, 1, false>(a, blocks, smem, st);
+    case 3: return launch_ws<MODEL, HIST, RECORD, false, 1, true>(a, blocks, smem, st);
+    case 4: return launch_ws<MODEL, HIST, RECORD, true, 0, false>(a, blocks, smem, st);
+    case 5: return launch_ws<MODEL, HIST, RECORD, true, 0, true>(a, blocks, smem, st);
+    case 6: return launch_ws<MODEL, HIST, RECORD, true, 1, false>(a, blocks, smem, st);
+    default: return launch_ws<MODEL, HIST, RECORD, true, 1, true>(a, blocks, smem, st);
     }
 }
 

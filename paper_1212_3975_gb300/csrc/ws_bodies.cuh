@@ -97,13 +97,59 @@ __device__ __forceinline__ WordCtx word_ctx(uint32_t R, uint32_t U, uint32_t D, 
     return x;
 }
 
+// Byte k of x, zero-extended / sign-extended (prmt: a selector nibble with its top bit
+// set replicates the sign of the byte it names).
+__device__ __forceinline__ uint32_t ubyte(uint32_t x, int k)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "r"(0x4440u | (uint32_t)k));
+    return d;
+}
+__device__ __forceinline__ uint32_t sbyte(uint32_t x, int k)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "r"((uint32_t)k | (8u | (uint32_t)k) * 0x1110u));
+    return d;
+}
+
+// Site constants of four consecutive sites of a word, one site per byte: the table
+// offsets 4 n0 / 4 n1 (n = number of unequal neighbours with the left neighbour old /
+// flipped) and the bin changes 40 - 20 n0 / 40 - 20 n1 (bytes of the table, 20 per
+// bin) as signed bytes.
+struct Quad {
+    uint32_t K0, K1, D0, D1;
+};
+
+// bits 4g..4g+3 of x, bit i to bit 8i + s
+__device__ __forceinline__ uint32_t spread4(uint32_t x, int g, int s)
+{
+    return (((x >> (4 * g)) & 0xFu) * (0x00204081u << s)) & (0x01010101u << s);
+}
+
+__device__ __forceinline__ Quad site_quad(const WordCtx &x, int g, bool rowstart)
+{
+    const uint32_t pre4 = spread4(x.lo, g, 2) + spread4(x.hi, g, 3);  // 4 x (up + down + right)
+    const uint32_t q4 = spread4(x.qw, g, 2);
+    Quad r;
+    r.K0 = pre4 + q4;
+    r.K1 = pre4 + 0x04040404u - q4;
+    // site 0 of a row: its left neighbour (site L-1) is not visited yet
+    if (rowstart) r.K1 = (r.K1 & 0xFFFFFF00u) | (r.K0 & 0xFFu);
+    // per byte 168 - 5 K >= 88: no borrow; xor 0x80 recentres to 40 - 20 n
+    r.D0 = (0xA8A8A8A8u - 5u * r.K0) ^ 0x80808080u;
+    r.D1 = (0xA8A8A8A8u - 5u * r.K1) ^ 0x80808080u;
+    return r;
+}
+
 // Ising decider for rows of whole words (L % 32 == 0, at least two words per row).
 // The sites of consecutive words form one software pipeline: while word it is decided,
 // the lattice words and neighbour planes of word it+1 are prepared, its first draws
 // are loaded (site 28) and the candidate thresholds of its site 0 are loaded with the
 // offsets resolved by site 30's decision (site 31), exactly as between sites of one
 // word.  (With one word per row the next word's upper neighbours are this word's new
-// spins, so that case keeps the per-word form.)
+// spins, so that case keeps the per-word form.)  The site constants come four sites
+// at a time in byte-parallel form, so a site costs four byte extractions, three
+// selects on the previous decision, three adds, the two loads and the compare.
 template <bool BOOK, bool TSMEM, int RU, int RS>
 __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t *lp, const size_t ls,
                                                     const uint32_t tab_s, const uint4 *s_ring, Snap *s_snap,
@@ -118,33 +164,16 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
     };
     auto row_up = [&](int y) { return (y == 0 ? L - 1 : y - 1) * RW; };    // row above: updated
     auto row_down = [&](int y) { return (y == L - 1 ? 0 : y + 1) * RW; };  // row below: old (new for y = L-1)
-    // constants of site j of a word: table addresses for the previous attempt rejected /
-    // accepted (left neighbour old / flipped) and the bin changes (x 20 bytes) if accepted
-    auto consts = [&](const WordCtx &x, int j, bool rowstart, bool rowend, uint32_t first_new, uint32_t &K0,
-                      uint32_t &K1, uint32_t &D0, uint32_t &D1) {
-        uint32_t pre = ((x.lo >> j) & 1u) + ((x.hi >> j) & 1u) * 2u;
-        if (j == 31) {
-            // row end: the right neighbour is site 0 of the row, already updated
-            const uint32_t pre_end = ((x.ua >> 31) & 1u) + ((x.ub >> 31) & 1u) + ((x.R >> 31) ^ first_new);
-            pre = rowend ? pre_end : pre;
-        }
-        const uint32_t q = (x.qw >> j) & 1u;
-        const uint32_t n0 = pre + q;
-        const uint32_t n1 = (j == 0 && rowstart) ? n0 : pre + 1u - q;
-        K0 = tab_s + 4u * n0;
-        K1 = tab_s + 4u * n1;
-        D0 = 40u - 20u * n0;
-        D1 = 40u - 20u * n1;
-    };
 
     // ---- word 0
     int y = 0, w = 0;
     WordCtx cur = word_ctx(LAT(0), LAT(row_up(0)), LAT(row_down(0)), LAT(1), (LAT(RW - 1) >> 31) & 1u);
     uint32_t first_new = 0u;
-    uint32_t P0 = bin20, P1 = bin20 + d20p;
-    uint32_t K0, K1, D0, D1;
-    consts(cur, 0, true, false, 0u, K0, K1, D0, D1);
-    uint32_t A0 = tload(P0 + K0), A1 = tload(P1 + K1);
+    // P0 / P1: table address of the current site's bin (tab_s + 20 bin) if the previous
+    // attempt was rejected / accepted
+    uint32_t P0 = tab_s + bin20, P1 = P0 + d20p;
+    Quad q0 = site_quad(cur, 0, true);
+    uint32_t A0 = tload(P0 + ubyte(q0.K0, 0)), A1 = tload(P1 + ubyte(q0.K1, 0));
     bar_sync(kBarFullU + 0, NU);
     uint4 blk = s_ring[lane], blk_next = s_ring[32 + lane];
 
@@ -153,6 +182,12 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
         const bool has_next = it + 1 < total;
         const int slot = it % RU;
         const uint4 *src = s_ring + slot * 8 * 32 + lane;
+        if (lastw) {
+            // the row's last site sees the updated site 0 as its right neighbour
+            const uint32_t tr2 = (cur.tr & 0x7FFFFFFFu) | (((cur.R >> 31) ^ first_new) << 31);
+            cur.lo = cur.ua ^ cur.ub ^ tr2;
+            cur.hi = (cur.ua & cur.ub) | (tr2 & (cur.ua ^ cur.ub));
+        }
         // next word: (y1, w1)
         int y1 = y, w1 = w + 1;
         if (w1 == RW) {
@@ -175,13 +210,18 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
         WordCtx nx;
         uint4 nblk = make_uint4(0u, 0u, 0u, 0u), nblk_next = nblk;
         uint32_t Rw = cur.R;
-        uint32_t K0n = 0u, K1n = 0u, D0n = 0u, D1n = 0u;
+        Quad q1 = site_quad(cur, 1, false);  // constants of the next four sites
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             const int k = j & 3;
             if (k == 0 && j > 0) {
                 blk = blk_next;
                 if (j < 28) blk_next = src[((j >> 2) + 1) * 32];
+                q0 = q1;
+                if (j < 28)
+                    q1 = site_quad(cur, (j >> 2) + 1, false);
+                else
+                    q1 = site_quad(nx, 0, w1 == 0);  // site 0 of the next word
             }
             if (j == 8) nx = word_ctx(R1, U1, D1w, Rn1, lb1);
             if (j == 28 && has_next) {
@@ -191,49 +231,38 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
                 nblk_next = src1[32];
             }
             const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
+            // this site's bin and its change if accepted, resolved by the previous decision
+            const uint32_t Pc = ap ? P1 : P0;
+            const uint32_t DD = ap ? sbyte(q0.D1, k) : sbyte(q0.D0, k);
+            const uint32_t nP1 = Pc + DD;
             // loads of the next site first (offsets resolved by the previous decision),
             // then the decision of this site
             uint32_t A0n = 0u, A1n = 0u;
-            const bool more = (j < 31) || has_next;
-            if (more) {
-                if (j < 31)
-                    consts(cur, j + 1, w == 0, lastw, first_new, K0n, K1n, D0n, D1n);
-                else
-                    consts(nx, 0, w1 == 0, false, 0u, K0n, K1n, D0n, D1n);
-                const uint32_t o0 = ap ? P1 + K0n : P0 + K0n;
-                const uint32_t o1 = ap ? P1 + D1 + K1n : P0 + D0 + K1n;
-                A0n = tload(o0);
-                A1n = tload(o1);
+            if ((j < 31) || has_next) {
+                const uint32_t K0n = k == 3 ? ubyte(q1.K0, 0) : ubyte(q0.K0, k + 1);
+                const uint32_t K1n = k == 3 ? ubyte(q1.K1, 0) : ubyte(q0.K1, k + 1);
+                A0n = tload(Pc + K0n);
+                A1n = tload(nP1 + K1n);
             }
             const uint32_t A = ap ? A1 : A0;
             const bool acc = u < A;
-            const uint32_t nP0 = ap ? P1 : P0;
-            const uint32_t nP1 = ap ? P1 + D1 : P0 + D0;
             A0 = A0n;
             A1 = A1n;
-            P0 = nP0;
+            P0 = Pc;
             P1 = nP1;
-            D0 = D0n;
-            D1 = D1n;
             Rw ^= acc ? (1u << j) : 0u;
             if (j == 0 && w == 0) first_new = (cur.R & 1u) ^ (acc ? 1u : 0u);
             ap = acc;
         }
+        q0 = q1;
         if (it < total - RU) bar_arrive(kBarEmptyU + slot, NU);
         LAT(y * RW + w) = Rw;
         if (BOOK) {
-            uint32_t lo = cur.lo, hi = cur.hi;
-            if (lastw) {
-                // the row's last site saw the updated site 0 as its right neighbour
-                const uint32_t tr2 = (cur.tr & 0x7FFFFFFFu) | (((cur.R >> 31) ^ first_new) << 31);
-                lo = cur.ua ^ cur.ub ^ tr2;
-                hi = (cur.ua & cur.ub) | (tr2 & (cur.ua ^ cur.ub));
-            }
             const int ss = it % RS;
             if (it >= RS) bar_sync(kBarEmptyS + ss, 64);
             Snap *sn = s_snap + ss * 32 + lane;
-            sn->lo = lo;
-            sn->hi = hi;
+            sn->lo = cur.lo;
+            sn->hi = cur.hi;
             sn->qw = cur.qw;
             sn->flip = cur.R ^ Rw;
             sn->rold = cur.R;
@@ -246,15 +275,23 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
         y = y1;
         w = w1;
     }
-    bin20 = P0;
+    bin20 = P0 - tab_s;
     d20p = P1 - P0;
 #undef LAT
 }
 
-template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+// HMODE: block histogram in global memory (0), in shared memory with one count per
+// attempt (1), or in shared memory with one count per pair of consecutive attempts
+// (2): C[b][d + 2] counts the pairs whose first attempt ends in bin b and whose second
+// ends in bin b + d (|d| <= 2), and the histogram is H[b] = sum_d C[b][d + 2] +
+// sum_d C[b - d][d + 2].  Mode 2 halves the shared-memory atomics, which otherwise
+// delay the decider's table loads.
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
 __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
     __syncthreads();  // smem may still be read by a previous work unit of this block
+    constexpr bool HSMEM = HMODE != 0;
+    constexpr bool HPAIR = HIST && HMODE == 2;
     constexpr bool BOOK = HIST || RECORD;
     constexpr int NP = BOOK ? 2 : 3;            // producer warps (one SM sub-partition each)
     constexpr int NT = 128;                     // decider + producers (+ bookkeeper)
@@ -262,8 +299,9 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     constexpr int BOOK_WARP = 1 + NP;
     const int n_tab = a.n_bins * 5;
     uint32_t *s_tab = smem;
+    const int n_hist = HPAIR ? a.n_bins * 5 : a.n_bins;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
-    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
+    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) : 0);
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [kRingU][8][32]
     Snap *s_snap = reinterpret_cast<Snap *>(s_ring + kRingU * 8 * 32);                   // [kRingS][32]
 
@@ -274,7 +312,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     if (TSMEM)
         for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
     if (HIST && HSMEM)
-        for (int i = tid; i < a.n_bins; i += NT) s_hist[i] = 0u;
+        for (int i = tid; i < n_hist; i += NT) s_hist[i] = 0u;
     if (LSMEM && warp == 0)
         for (int k = 0; k < a.lat_words; ++k) s_lat[k * 32 + lane] = a.lat[(size_t)k * a.p_pad + c];
     // production launches: magnetisation at the start, read before the decider
@@ -556,7 +594,26 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                             }
                         }
                     };
-                    if (nb == 32) {
+                    if (HPAIR) {
+                        // one count per pair of attempts (nb is a multiple of 4)
+                        auto delta = [&](int j) {
+                            const int nneq =
+                                (int)(((sn.lo >> j) & 1u) + 2u * ((sn.hi >> j) & 1u) + ((qn >> j) & 1u));
+                            return ((sn.flip >> j) & 1u) ? 2 - nneq : 0;
+                        };
+                        auto book_pair = [&](int j) {
+                            bin += delta(j);
+                            const int d = delta(j + 1);
+                            if (active) red_shared(s_hist + 5 * bin + 2 + d, 1u);
+                            bin += d;
+                        };
+                        if (nb == 32) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 2) book_pair(j);
+                        } else {
+                            for (int j = 0; j < nb; j += 2) book_pair(j);
+                        }
+                    } else if (nb == 32) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) book_site(j);
                     } else {
@@ -596,7 +653,18 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         for (int k = 0; k < a.lat_words; ++k) up += __popc(a.lat[(size_t)k * a.p_pad + c]);
         a.M[c] = 2 * up - V;
     }
-    if (HIST && HSMEM) {
+    if (HPAIR) {
+        // first attempts of the pairs in bin b, then second attempts (from bin b - d)
+        for (int b = tid; b < a.n_bins; b += NT) {
+            uint32_t v = 0u;
+#pragma unroll
+            for (int d = -2; d <= 2; ++d) {
+                v += s_hist[5 * b + 2 + d];
+                if (b - d >= 0 && b - d < a.n_bins) v += s_hist[5 * (b - d) + 2 + d];
+            }
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[b]), (unsigned long long)v);
+        }
+    } else if (HIST && HSMEM) {
         for (int i = tid; i < a.n_bins; i += NT) {
             const uint32_t v = s_hist[i];
             if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[i]), (unsigned long long)v);
