@@ -97,7 +97,7 @@ struct SweepArgs {
 // staging flags of a sweep launch
 struct SweepPlan {
     bool table_smem, hist_smem, lattice_smem;
-    bool hist_pairs;        // Ising warp-specialised: shared histogram of attempt pairs
+    bool hist_pairs;        // warp-specialised: shared histogram of attempt pairs
     bool warp_specialized;  // decider / producer / bookkeeper warps per 32 chains
     int chains_per_block;
     size_t smem_bytes;

@@ -467,11 +467,11 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs)
     const int staging = ctx->cfg.staging;
     pl.lattice_smem = staging == MUCA_STAGING_SHARED || (staging == MUCA_STAGING_AUTO && used + lat <= cap);
     if (pl.lattice_smem) used += lat;
-    // Ising warp-specialised launches: the histogram of attempt pairs (5 counts per
-    // bin) when it fits beside the table and the lattices
-    const size_t pairs = ((size_t)ctx->n_bins * 5 * 4 + 15) & ~(size_t)15;
-    pl.hist_pairs = allow_pairs && ws && ctx->model == MUCA_ISING && pl.table_smem && pl.hist_smem &&
-                    pl.lattice_smem && used - hist + pairs <= cap;
+    // warp-specialised launches: the histogram of attempt pairs (one count per bin
+    // change of a single attempt: 5 for Ising, 9 for Potts) when it fits beside the
+    // table and the lattices
+    const size_t pairs = ((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15;
+    pl.hist_pairs = allow_pairs && ws && pl.table_smem && pl.hist_smem && pl.lattice_smem && used - hist + pairs <= cap;
     if (pl.hist_pairs) used += pairs - hist;
     pl.smem_bytes = used;
     return pl;

@@ -13,20 +13,20 @@ __global__ void __launch_bounds__(128) ising_ws_kernel(SweepArgs a)
 }
 
 // iteration and production launches: five warps (decider, 3 producers, bookkeeper)
-template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM>
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
 __global__ void __launch_bounds__(160) potts_ws_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    potts_ws_body<HIST, RECORD, TSMEM, HSMEM, LSMEM, true>(a, blockIdx.x, smem);
+    potts_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM, true>(a, blockIdx.x, smem);
 }
 
 // HMODE: histogram in global memory (0), shared per attempt (1), shared per pair of
-// attempts (2, Ising only)
+// attempts (2)
 template <int MODEL, bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
 cudaError_t launch_ws(const SweepArgs &a, int blocks, size_t smem, cudaStream_t st)
 {
     auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM>
-                                    : potts_ws_kernel<HIST, RECORD, TSMEM, HMODE != 0, LSMEM>;
+                                    : potts_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -39,7 +39,7 @@ template <int MODEL, bool HIST, bool RECORD>
 cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size_t smem, cudaStream_t st)
 {
     // pair histogram: planned only with the table and the lattices in shared memory
-    if (MODEL == MUCA_ISING && HIST && pl.hist_smem && pl.hist_pairs)
+    if (HIST && pl.hist_smem && pl.hist_pairs)
         return launch_ws<MODEL, HIST, RECORD, true, 2, true>(a, blocks, smem, st);
     const int key = (pl.table_smem ? 4 : 0) | ((HIST && pl.hist_smem) ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
     switch (key) {

@@ -733,20 +733,24 @@ __device__ __forceinline__ void potts_count_word(uint32_t word, uint32_t (&cnt)[
 // records from per-word snapshots (iteration and production launches of the
 // standalone kernel); the decider then runs on warp 1, alone on its SM sub-partition,
 // and the bookkeeper shares one with producer warp 0.
-template <bool HIST, bool RECORD, bool TSMEM, bool HSMEM, bool LSMEM, bool PBOOK = false>
+// HMODE as for Ising; in mode 2 (bookkeeper only) C[b][d + 4] counts the pairs of
+// consecutive attempts ending in bins b and b + d (|d| <= 4).
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, bool PBOOK = false>
 __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
+    constexpr bool HSMEM = HMODE != 0;
     constexpr bool BOOKW = PBOOK && (HIST || RECORD);
+    constexpr bool HPAIR = BOOKW && HIST && HMODE == 2;
     constexpr int NT = BOOKW ? 160 : 128;  // decider + one producer warp per ring slot (+ bookkeeper)
     constexpr int NU = 64;                 // decider + the slot's producer
     __syncthreads();  // smem may still be read by a previous work unit of this block
     const int n_tab = a.n_bins * 9;
     uint32_t *s_tab = smem;
+    const int n_hist = HPAIR ? a.n_bins * 9 : a.n_bins;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
-    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((a.n_bins + 3) & ~3) : 0);
+    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) : 0);
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][8 words][2][32]
     uint4 *s_psnap = s_ring + kPottsRing * 16 * 32;                                      // [kRingS][2][32]
-    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_psnap + kRingS * 2 * 32);          // [8][32] state counts
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vw = BOOKW ? (warp == 0 ? 1 : warp == 1 ? 0 : warp) : warp;  // role: 0 decider, 1..3 producers, 4 bookkeeper
@@ -756,17 +760,21 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     if (TSMEM)
         for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
     if (HIST && HSMEM)
-        for (int i = tid; i < a.n_bins; i += NT) s_hist[i] = 0u;
+        for (int i = tid; i < n_hist; i += NT) s_hist[i] = 0u;
     if (LSMEM && vw == 0)
         for (int k = 0; k < a.lat_words; ++k) s_lat[k * 32 + lane] = a.lat[(size_t)k * a.p_pad + c];
     // bookkeeper of a production launch: state counts of the starting lattice, read
-    // before the decider changes it, one shared-memory counter per state and lane
+    // before the decider changes it (16-bit counters, four per register)
     const int bk_bin0 = active ? a.E[c] + 2 * a.L * a.L : a.L * a.L;  // bin at the start
+    uint64_t bk_lo = 0, bk_hi = 0;
     if (BOOKW && RECORD && vw == 4) {
         uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int k = 0; k < a.lat_words; ++k) potts_count_word(a.lat[(size_t)k * a.p_pad + c], cnt);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s_cnt[k * 32 + lane] = cnt[k];
+        for (int k = 0; k < 4; ++k) {
+            bk_lo |= (uint64_t)cnt[k] << (16 * k);
+            bk_hi |= (uint64_t)cnt[k + 4] << (16 * k);
+        }
     }
     __syncthreads();
 
@@ -1063,7 +1071,14 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             if (HIST) pb = sn[0];
             if (RECORD) rs = sn[32];
             if (q < total_words - kRingS) bar_arrive(kBarEmptyS + ss, 64);
-            if (HIST) {
+            if (HPAIR) {
+                // one count per pair of attempts: (0, 1) and (2, 3)
+                const int b0 = bin_of(pb.x), b1 = bin_of(pb.y), b2 = bin_of(pb.z), b3 = bin_of(pb.w);
+                if (active) {
+                    red_shared(s_hist + 9 * b0 + 4 + (b1 - b0), 1u);
+                    red_shared(s_hist + 9 * b2 + 4 + (b3 - b2), 1u);
+                }
+            } else if (HIST) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int bin = bin_of(k == 0 ? pb.x : k == 1 ? pb.y : k == 2 ? pb.z : pb.w);
@@ -1083,21 +1098,18 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             }
             if (RECORD) {
                 // rs = (bin row after the word's last attempt, old spins, proposals, accepted bytes)
-                // accepted sites move one count from the old state to the new one
+                // accepted sites move one count from the old state to the new one; a
+                // rejected site moves one from state 0 to state 0 (no branch)
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if ((rs.w >> (8 * k)) & 1u) {
-                        red_shared(s_cnt + byte_of(rs.y, k) * 32 + lane, 0xFFFFFFFFu);
-                        red_shared(s_cnt + byte_of(rs.z, k) * 32 + lane, 1u);
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    const bool acc = (rs.w >> (8 * k)) & 1u;
+                    potts_count_move(bk_lo, bk_hi, acc ? byte_of(rs.y, k) : 0u, acc ? byte_of(rs.z, k) : 0u);
+                }
                 if ((q + 1) % words_per_sweep == 0 && active) {
                     const int sw = q / words_per_sweep;
                     const int bin = bin_of(rs.x);
                     const int E = bin - 2 * V;
-                    uint32_t mx = 0;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) mx = max(mx, s_cnt[k * 32 + lane]);
-                    const int M = 8 * (int)mx - V;
+                    const int M = 8 * potts_count_max(bk_lo, bk_hi) - V;
                     if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
                     if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
                     if (a.samples) {
@@ -1114,24 +1126,26 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             if (HIST && !HSMEM && run)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
             if (RECORD) {
-                uint64_t lo = 0, hi = 0;
-                uint32_t mx = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t c0 = s_cnt[k * 32 + lane], c1 = s_cnt[(k + 4) * 32 + lane];
-                    lo |= (uint64_t)c0 << (16 * k);
-                    hi |= (uint64_t)c1 << (16 * k);
-                    mx = max(mx, max(c0, c1));
-                }
-                a.M[c] = 8 * (int)mx - V;
-                a.cnt[c] = lo;
-                a.cnt[a.p_pad + c] = hi;
+                a.M[c] = 8 * potts_count_max(bk_lo, bk_hi) - V;
+                a.cnt[c] = bk_lo;
+                a.cnt[a.p_pad + c] = bk_hi;
             }
         }
     }
 #undef LAT
     __syncthreads();
-    if (HIST && HSMEM) {
+    if (HPAIR) {
+        // first attempts of the pairs in bin b, then second attempts (from bin b - d)
+        for (int b = tid; b < a.n_bins; b += NT) {
+            uint32_t v = 0u;
+#pragma unroll
+            for (int d = -4; d <= 4; ++d) {
+                v += s_hist[9 * b + 4 + d];
+                if (b - d >= 0 && b - d < a.n_bins) v += s_hist[9 * (b - d) + 4 + d];
+            }
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[b]), (unsigned long long)v);
+        }
+    } else if (HIST && HSMEM) {
         for (int i = tid; i < a.n_bins; i += NT) {
             const uint32_t v = s_hist[i];
             if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[i]), (unsigned long long)v);
@@ -1143,8 +1157,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
 // the bookkeeper, its snapshot ring
 __host__ __device__ constexpr size_t potts_ws_extra_smem(bool book = false)
 {
-    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) +
-           (book ? (size_t)kRingS * 2 * 32 * sizeof(uint4) + 8 * 32 * sizeof(uint32_t) : 0);
+    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) + (book ? (size_t)kRingS * 2 * 32 * sizeof(uint4) : 0);
 }
 }  // namespace ws
 }  // namespace muca
