@@ -499,12 +499,13 @@ def batched_comparison(m, torch):
 INST_PER_ATTEMPT_ISING_L64 = 2.07
 # dram__bytes_read.sum + dram__bytes_write.sum of one weight-iteration launch of the same
 # kernel (staging of table, histogram and lattices only; independent of the sweep count)
-TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = 685568
+TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = None
 # l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / attempts of the same capture
 SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 = 0.38
 # cycles per site of the decider's 32-site loop run alone on one warp (a replica of the
-# loop with the same table, draws and dependency structure, clock64-timed on a GB300)
-DECIDER_CYCLES_PER_ATTEMPT_ALONE = 43.1
+# loop with the same table, draws, byte-parallel site constants and dependency
+# structure, clock64-timed on a GB300)
+DECIDER_CYCLES_PER_ATTEMPT_ALONE = 36.6
 
 
 def run_probe(args):
