@@ -496,12 +496,12 @@ def batched_comparison(m, torch):
 
 # measured with ncu (inst_executed / attempts) on the weight-iteration sweep kernel of
 # the 64x64 Ising workload; see profiles/
-INST_PER_ATTEMPT_ISING_L64 = 2.07
+INST_PER_ATTEMPT_ISING_L64 = 1.89
 # dram__bytes_read.sum + dram__bytes_write.sum of one weight-iteration launch of the same
 # kernel (staging of table, histogram and lattices only; independent of the sweep count)
-TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = None
+TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = 682240
 # l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / attempts of the same capture
-SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 = 0.38
+SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 = 0.354
 # cycles per site of the decider's 32-site loop run alone on one warp (a replica of the
 # loop with the same table, draws, byte-parallel site constants and dependency
 # structure, clock64-timed on a GB300)
