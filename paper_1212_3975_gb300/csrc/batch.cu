@@ -57,27 +57,35 @@ __device__ __forceinline__ SweepArgs batch_args(const BatchJob &j, int n_sweeps,
     return a;
 }
 
-template <int MODEL, bool HIST, bool T, bool H, bool Lt>
+// H: histogram mode (0 global, 1 shared per attempt, 2 shared per pair of attempts;
+// the Potts body without a bookkeeper warp counts per attempt)
+template <int MODEL, bool HIST, bool T, int H, bool Lt>
 __device__ __forceinline__ void body(const SweepArgs &a, int cblk, uint32_t *smem)
 {
     if (MODEL == MUCA_ISING)
-        ising_ws_body<HIST, false, T, H && HIST, Lt>(a, cblk, smem);
+        ising_ws_body<HIST, false, T, HIST ? H : 0, Lt>(a, cblk, smem);
     else
-        potts_ws_body<HIST, false, T, H && HIST, Lt>(a, cblk, smem);
+        potts_ws_body<HIST, false, T, (HIST && H) ? 1 : 0, Lt>(a, cblk, smem);
 }
 
 template <int MODEL, bool HIST>
 __device__ __forceinline__ void run_unit(const SweepArgs &a, int flags, int cblk, uint32_t *smem)
 {
-    switch (flags) {
-    case 0: body<MODEL, HIST, false, false, false>(a, cblk, smem); break;
-    case 1: body<MODEL, HIST, false, false, true>(a, cblk, smem); break;
-    case 2: body<MODEL, HIST, false, true, false>(a, cblk, smem); break;
-    case 3: body<MODEL, HIST, false, true, true>(a, cblk, smem); break;
-    case 4: body<MODEL, HIST, true, false, false>(a, cblk, smem); break;
-    case 5: body<MODEL, HIST, true, false, true>(a, cblk, smem); break;
-    case 6: body<MODEL, HIST, true, true, false>(a, cblk, smem); break;
-    default: body<MODEL, HIST, true, true, true>(a, cblk, smem); break;
+    if constexpr (MODEL == MUCA_ISING) {
+        if (flags & 8) {  // histogram of attempt pairs (table and lattices staged)
+            body<MODEL, HIST, true, 2, true>(a, cblk, smem);
+            return;
+        }
+    }
+    switch (flags & 7) {
+    case 0: body<MODEL, HIST, false, 0, false>(a, cblk, smem); break;
+    case 1: body<MODEL, HIST, false, 0, true>(a, cblk, smem); break;
+    case 2: body<MODEL, HIST, false, 1, false>(a, cblk, smem); break;
+    case 3: body<MODEL, HIST, false, 1, true>(a, cblk, smem); break;
+    case 4: body<MODEL, HIST, true, 0, false>(a, cblk, smem); break;
+    case 5: body<MODEL, HIST, true, 0, true>(a, cblk, smem); break;
+    case 6: body<MODEL, HIST, true, 1, false>(a, cblk, smem); break;
+    default: body<MODEL, HIST, true, 1, true>(a, cblk, smem); break;
     }
 }
 
@@ -221,12 +229,24 @@ int configure(muca_batch *b)
     b->smem = 0;
     b->max_bins = b->max_thr = b->max_ktab = 0;
     std::vector<std::pair<long long, BatchUnit>> units;
+    // Every block gets the shared memory of the largest job, so the histogram of
+    // attempt pairs is used only where it does not raise that maximum (more shared
+    // memory leaves less L1 to the jobs that read their tables from global memory).
+    size_t smem_plain = 0;
+    for (int i = 0; i < b->n_jobs; ++i) {
+        b->ctx[i]->cfg.staging = b->staging;
+        const SweepPlan pl = plan_sweeps(b->ctx[i], false);
+        smem_plain = std::max(smem_plain, pl.smem_bytes + ws_extra_smem(b->ctx[i]->model));
+    }
     for (int i = 0; i < b->n_jobs; ++i) {
         muca_ctx *c = b->ctx[i];
         c->cfg.staging = b->staging;
         if (c->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
             return fail(MUCA_ERR_ARG, "batched lattices need the energy ensemble (job " + std::to_string(i) + ")");
-        const SweepPlan pl = plan_sweeps(c, false);  // the batched kernel counts per attempt
+        // pairs of attempts for Ising (its body has a bookkeeper warp here) within the
+        // shared memory of the largest job; the batched Potts body counts per attempt
+        SweepPlan pl = plan_sweeps(c, c->model == MUCA_ISING);
+        if (pl.hist_pairs && pl.smem_bytes + ws_extra_smem(c->model) > smem_plain) pl = plan_sweeps(c, false);
         if (!pl.warp_specialized)
             return fail(MUCA_ERR_ARG, "batched lattices need L % 4 == 0 (job " + std::to_string(i) + ")");
         BatchJob &j = b->h_jobs[i];
@@ -261,7 +281,7 @@ int configure(muca_batch *b)
         j.conv = b->d_conv + i;
         j.ctr3_therm = ((uint32_t)(c->seed >> 32) << 2) | kPhaseThermalize;
         j.therm = b->d_therm + i;
-        j.flags = (pl.table_smem ? 4 : 0) | (pl.hist_smem ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
+        j.flags = (pl.hist_pairs ? 8 : 0) | (pl.table_smem ? 4 : 0) | (pl.hist_smem ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
         b->smem = std::max(b->smem, pl.smem_bytes + ws_extra_smem(c->model));
         b->max_bins = std::max(b->max_bins, c->n_bins);
         b->max_thr = std::max(b->max_thr, c->n_bins * c->n_de);
