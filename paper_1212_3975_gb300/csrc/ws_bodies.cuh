@@ -371,7 +371,8 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         uint32_t *lp = LSMEM ? s_lat + lane : a.lat + c;
         const size_t ls = LSMEM ? (size_t)32 : (size_t)a.p_pad;
 #define LAT(k) lp[(size_t)(k) * ls]
-        const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
+        // table addresses: shared-memory addresses, or byte offsets into the global table
+        const uint32_t tab_s = TSMEM ? (uint32_t)__cvta_generic_to_shared(s_tab) : 0u;
 #define TAB_BYTES(o)                 \
     (TSMEM ? lds_u32(tab_s + (o))    \
            : ldg_nc_u32(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + (o))))
@@ -847,7 +848,8 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
         }
     } else if (vw == 0) {
         // ---------------- decider ------------------------------------------------
-        const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
+        // table addresses: shared-memory addresses, or byte offsets into the global table
+        const uint32_t tab_s = TSMEM ? (uint32_t)__cvta_generic_to_shared(s_tab) : 0u;
         const char *tab_g = reinterpret_cast<const char *>(a.ktab) - tab_s;
 #define TABLOAD(o) (TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(tab_g + (o))))
         const int bin0 = active ? a.E[c] + 2 * V : V;
@@ -1057,7 +1059,8 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
     } else if (BOOKW && vw == 4) {
         // ---------------- bookkeeper: histogram, state counts, records -----------
-        const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(s_tab);
+        // table addresses: shared-memory addresses, or byte offsets into the global table
+        const uint32_t tab_s = TSMEM ? (uint32_t)__cvta_generic_to_shared(s_tab) : 0u;
         auto bin_of = [&](uint32_t P) { return (int)(((P - tab_s) >> 2) * 0x38E38E39u); };
         int run_bin = bk_bin0;
         uint32_t run = 0;
