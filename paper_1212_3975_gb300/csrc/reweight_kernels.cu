@@ -165,6 +165,38 @@ __global__ void __launch_bounds__(256) reweight_fp64_kernel(BinData d, const dou
 }
 
 // ------------------------------ FP32 -------------------------------------------
+// FP64 shift of every beta of a tile, one warp per beta at a time: c_t = (lnO_T - beta_t
+// E_T) - max_b (lnO_b - beta_t E_b) over the window, in log2 units, and beta_t - beta_T.
+// The maximum is exact, so the order of the reduction does not change it.
+template <int TILE>
+__device__ void tile_shifts(const BinData &d, const double *betas, int j0, int nt, int lo, int hi, double lnOT,
+                            double ET, double betaT, float *s_c, float *s_db)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = warp; t < TILE; t += nw) {
+        if (t >= nt) {
+            if (lane == 0) {
+                s_c[t] = -1e30f;
+                s_db[t] = 0.f;
+            }
+            continue;
+        }
+        const double beta = betas[j0 + t];
+        double m = -INFINITY;
+#pragma unroll 4
+        for (int b = lo + lane; b <= hi; b += 32) {
+            const double l = d.lnO[b];
+            if (l != -INFINITY) m = fmax(m, __dsub_rn(l, __dmul_rn(beta, d.E[b])));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            s_c[t] = (float)(((lnOT - beta * ET) - m) * kLog2e);
+            s_db[t] = (float)((beta - betaT) * kLog2e);
+        }
+    }
+    __syncthreads();
+}
+
 template <int TILE>
 __global__ void __launch_bounds__(256) reweight_fp32_kernel(BinData d, const double *betas, int n_beta,
                                                             int n_bins, int V, double mnorm, Observables o)
@@ -212,24 +244,7 @@ __global__ void __launch_bounds__(256) reweight_fp32_kernel(BinData d, const dou
     }
 
     // FP64 shift of every beta of the tile (maximum lies inside the window)
-    for (int t = 0; t < nt; ++t) {
-        const double beta = betas[j0 + t];
-        double m = -INFINITY;
-        int mi = n_bins;
-        for (int b = lo + (int)threadIdx.x; b <= hi; b += blockDim.x) {
-            const double l = d.lnO[b];
-            if (l == -INFINITY) continue;
-            const double a = __dsub_rn(l, __dmul_rn(beta, d.E[b]));
-            if (a > m || (a == m && b < mi)) { m = a; mi = b; }
-        }
-        block_argmax(m, mi, s_val, s_idx);
-        if (threadIdx.x == 0) {
-            const double c = (lnOT - beta * ET) - m;  // <= 0
-            s_c[t] = (float)(c * kLog2e);
-            s_db[t] = (float)((beta - betaT) * kLog2e);
-        }
-    }
-    __syncthreads();
+    tile_shifts<TILE>(d, betas, j0, nt, lo, hi, lnOT, ET, betaT, s_c, s_db);
     float cj[TILE], dbj[TILE];
 #pragma unroll
     for (int t = 0; t < TILE; ++t) {
@@ -330,27 +345,7 @@ __device__ void tile_prologue(const BinData &d, const double *betas, int n_beta,
     int i2 = 0;
     block_argmax(v2, i2, s_val, s_idx);
     hi = (int)v2;
-    for (int t = 0; t < TILE; ++t) {
-        if (t >= nt) {
-            if (threadIdx.x == 0) { s_c[t] = -1e30f; s_db[t] = 0.f; }
-            continue;
-        }
-        const double beta = betas[j0 + t];
-        double m = -INFINITY;
-        int mi = n_bins;
-        for (int b = lo + (int)threadIdx.x; b <= hi; b += blockDim.x) {
-            const double l = d.lnO[b];
-            if (l == -INFINITY) continue;
-            const double a = __dsub_rn(l, __dmul_rn(beta, d.E[b]));
-            if (a > m || (a == m && b < mi)) { m = a; mi = b; }
-        }
-        block_argmax(m, mi, s_val, s_idx);
-        if (threadIdx.x == 0) {
-            s_c[t] = (float)(((lnOT - beta * ET) - m) * kLog2e);
-            s_db[t] = (float)((beta - betaT) * kLog2e);
-        }
-    }
-    __syncthreads();
+    tile_shifts<TILE>(d, betas, j0, nt, lo, hi, lnOT, ET, betaT, s_c, s_db);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float first, float second)
