@@ -5,18 +5,20 @@
 //
 // Within one chain every attempt depends on the previous one (the weight depends on
 // the global energy), so a chain's speed is set by the length of its own instruction
-// stream.  This kernel therefore splits the work of each group of 32 chains over
-// three warps of one block, each on its own scheduler:
+// stream.  This kernel therefore splits the work of each group of 32 chains over the
+// four warps of one block, each on its own scheduler:
 //   warp 0 (decider): the Markov chain proper -- neighbour sums, threshold load,
 //          accept, spin flip.  The table offset for an attempt is chosen between two
 //          candidates prepared before the previous accept is known, and both
 //          candidate thresholds are loaded speculatively, so only a select and one
 //          compare lie between consecutive decisions.
-//   warp 1 (producer): the Philox4x32-10 draws (independent of the chain state) of
-//          each row word, written to a shared-memory ring ahead of the decider.
-//   warp 2 (bookkeeper, iteration and production launches): rebuilds from a
+//   warps 1..3 (producers; 1..2 when warp 3 keeps the books): the Philox4x32-10
+//          draws (independent of the chain state) of each row word, written to a
+//          shared-memory ring ahead of the decider.
+//   warp 3 (bookkeeper, iteration and production launches): rebuilds from a
 //          per-word snapshot (neighbour sums, flip mask) every attempt's energy bin,
-//          fills the block histogram, and writes the (E, M) records.
+//          fills the block histogram (one count per attempt, or per pair of
+//          consecutive attempts), and writes the (E, M) records.
 // Hand-offs use named barriers (bar.sync / bar.arrive) in the classic full/empty
 // pattern; every warp runs the same (sweep, row, word) loop nest, so the number of
 // arrivals and waits on each barrier match exactly.
