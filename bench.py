@@ -19,6 +19,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -72,11 +73,13 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # raw samples: MUCA_CLOCKS_CSV if set (kept), else a temporary file
+        self.path = os.environ.get("MUCA_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "muca_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(self.path) or ".", exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
@@ -96,7 +99,11 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         sm, mx, reasons = [], [], set()
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        if not os.environ.get("MUCA_CLOCKS_CSV"):
+            os.remove(self.path)
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 4:
                 continue
