@@ -365,14 +365,16 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__global__ void __launch_bounds__(128) reweight_bf16_kernel(BinData d, const double *betas, int n_beta, int n_bins,
-                                                            int V, double mnorm, Observables o)
+constexpr int kBf16Warps = 8;  // warps per tile of 16 betas (each takes every 8th chunk of 16 bins)
+
+__global__ void __launch_bounds__(32 * kBf16Warps) reweight_bf16_kernel(BinData d, const double *betas, int n_beta,
+                                                                        int n_bins, int V, double mnorm, Observables o)
 {
-    constexpr int TILE = 16;
+    constexpr int TILE = 16, NW = kBf16Warps;
     __shared__ double s_val[32 * 6];
     __shared__ int s_idx[32];
     __shared__ float s_c[TILE], s_db[TILE];
-    __shared__ double s_red[4][TILE][8];
+    __shared__ double s_red[NW][TILE][8];
     const int j0 = blockIdx.x * TILE;
     const int nt = min(TILE, n_beta - j0);
     double lnOT, ET, x1T, betaT;
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(128) reweight_bf16_kernel(BinData d, const dou
     const float c0 = s_c[g], db0 = s_db[g], c1 = s_c[g + 8], db1 = s_db[g + 8];
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     double accd[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int base = lo + 16 * warp; base <= hi; base += 64) {
+    for (int base = lo + 16 * warp; base <= hi; base += 16 * NW) {
         // each lane prepares one bin of the chunk (lanes 16..31 repeat lanes 0..15)
         const int b = base + (lane & 15);
         float G = -1e30f, dE = 0.f, dx = 0.f, vb = 0.f;
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(128) reweight_bf16_kernel(BinData d, const dou
     if ((int)threadIdx.x < nt) {
         const int t = threadIdx.x;
         double S[6] = {0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < 4; ++w)
+        for (int w = 0; w < NW; ++w)
             for (int k = 0; k < 6; ++k) S[k] += s_red[w][t][k];
         write_obs(o, j0 + t, betas[j0 + t], ET, x1T, S[0], S[1], S[2], S[3], S[4], S[5], V, mnorm);
     }
@@ -502,7 +504,8 @@ int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precis
         reweight_fp32_kernel<8><<<tiles, 256, 0, ctx->stream>>>(d, d_betas, n_beta, ctx->n_bins, ctx->V, mnorm, o);
     } else if (precision == MUCA_BF16) {
         const int tiles = (n_beta + 15) / 16;
-        reweight_bf16_kernel<<<tiles, 128, 0, ctx->stream>>>(d, d_betas, n_beta, ctx->n_bins, ctx->V, mnorm, o);
+        reweight_bf16_kernel<<<tiles, 32 * kBf16Warps, 0, ctx->stream>>>(d, d_betas, n_beta, ctx->n_bins, ctx->V,
+                                                                         mnorm, o);
     } else {
         return fail(MUCA_ERR_ARG, "precision must be MUCA_FP64, MUCA_FP32 or MUCA_BF16");
     }
