@@ -48,3 +48,30 @@ def test_single_rank_passthrough():
     import bench
     assert bench.max_over_ranks([1.0, 2.0], 1, "cpu") == [1.0, 2.0]
     assert bench.whole_job_rate(4e9, 1, 2.0) == pytest.approx(2.0)
+
+
+def test_clock_sampler_summary(tmp_path, monkeypatch):
+    """The clock summary of the bench line: median and maximum SM clock and every
+    active throttle reason but idle, from nvidia-smi's CSV (here a stand-in script)."""
+    import time
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '1980, 2070, 1200.5, 0x0000000000000004'\n"
+                    "echo '2070, 2070, 1300.0, 0x0000000000000001'\n"
+                    "echo '2070, 2070, 1310.0, 0x0000000000000028'\n"
+                    "echo 'N/A, N/A, N/A, N/A'\n"
+                    "sleep 5\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    monkeypatch.delenv("MUCA_CLOCKS_CSV", raising=False)
+    c = bench.ClockSampler(0)
+    c.start()
+    for _ in range(50):
+        if os.path.exists(c.path) and os.path.getsize(c.path) > 100:
+            break
+        time.sleep(0.05)
+    r = c.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3,
+                 "reasons": ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]}
+    assert not os.path.exists(c.path)  # temporary samples are removed
