@@ -195,21 +195,27 @@ int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
  * want observables -- e.g. an application whose framework allocator already holds
  * the free device memory, or a latency-critical loop that must not stall on
  * cudaMalloc/cudaFree (cudaFree synchronises the device).
- * It computes what muca_reweight computes (Eq. 2, same outputs, same kernels) from
+ * In FP64 or FP32 it computes what muca_reweight computes (Eq. 2, same outputs, same
+ * kernels; BF16 is not offered here) from
  * caller-owned DEVICE buffers, without a context:
  *   samples [3][n_bins] uint64 (count, sum |M|, sum M^2 per bin, as muca_get_samples),
  *   lnw [n_bins] FP64 (the weights the samples were produced with), betas [n_beta],
  *   out [4][n_beta] FP64 (rows e, C, absm, chi); precision MUCA_FP64 or MUCA_FP32;
  *   work is queued on cuda_stream (NULL = legacy default stream).
  * Its scratch is one fixed array inside the library's device image, 5 x 16385
- * doubles (655,400 bytes), present on every GPU that loads the library until the
- * process exits; lattices with more than 16385 bins (Ising L > 128, 8-Potts L > 90)
- * are rejected with MUCA_ERR_ARG.  The first call on a device looks the array's
- * address up (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that overlap on the
- * GPU (e.g. on two streams) race and give wrong results; serialise them.  Each call
- * writes every scratch entry it reads, so nothing needs clearing between calls.
- * Errors: MUCA_ERR_ARG (bad model/size, host pointers, too many bins), MUCA_ERR_CUDA. */
+ * doubles (655,400 bytes); lattices with more than 16385 bins (Ising L > 128,
+ * 8-Potts L > 90) are rejected with MUCA_ERR_ARG.  The image, and with it the array,
+ * is loaded onto a GPU by the first call on that device (CUDA loads modules lazily
+ * by default), so that first call needs 655,400 bytes of free device memory once and
+ * can fail with MUCA_ERR_CUDA when none is left: make it at start-up, before any
+ * stream capture.  From then on the GPU holds the array until the process exits.
+ * Every call looks the array's address up for the current device and context
+ * (cudaGetSymbolAddress), so a device reset is harmless.  All calls share the array:
+ * calls that overlap on the GPU (e.g. on two streams) race and give wrong results;
+ * serialise them.  Each call writes every scratch entry it reads, so nothing needs
+ * clearing between calls.  Only MUCA_FP64 and MUCA_FP32 are supported.
+ * Errors: MUCA_ERR_ARG (bad model/size, precision, host pointers or buffers of
+ * another device, too many bins), MUCA_ERR_CUDA. */
 int muca_reweight_noalloc(int model, int L, int q, const uint64_t *samples, const double *lnw,
                           const double *betas, int n_beta, int precision, double *out,
                           void *cuda_stream);
@@ -275,6 +281,18 @@ int muca_batch_converge(muca_batch *b, int n_sweeps, int therm_sweeps, int max_i
 
 /* The context of job j (owned by the batch; use it for state access). */
 muca_ctx *muca_batch_job(muca_batch *b, int j);
+
+/* How the persistent sweep kernel stages job j (as configured by muca_batch_create
+ * or the last muca_batch_autotune): a bit mask, MUCA_BATCH_PAIR_HIST (histogram of
+ * pairs of consecutive attempts), MUCA_BATCH_TABLE_SMEM (threshold table in shared
+ * memory; otherwise read from global memory), MUCA_BATCH_HIST_SMEM (block histogram
+ * in shared memory), MUCA_BATCH_LATTICE_SMEM (lattices in shared memory).
+ * Errors: MUCA_ERR_ARG (no such job). */
+#define MUCA_BATCH_LATTICE_SMEM 1
+#define MUCA_BATCH_HIST_SMEM 2
+#define MUCA_BATCH_TABLE_SMEM 4
+#define MUCA_BATCH_PAIR_HIST 8
+int muca_batch_plan(const muca_batch *b, int j);
 
 /* Pick the persistent grid size, the lattice staging and the number of sweep
  * launches per iteration by timing one iteration of n_sweeps on a scratch copy of

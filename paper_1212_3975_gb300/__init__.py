@@ -10,8 +10,8 @@ import ctypes
 import numpy as np
 
 from ._muca import (  # noqa: F401
-    MUCA_BF16, MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION, MUCA_FP32, MUCA_FP64, MUCA_ISING,
-    MUCA_POTTS, MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL,
+    MUCA_BATCH_HIST_SMEM, MUCA_BATCH_LATTICE_SMEM, MUCA_BATCH_PAIR_HIST, MUCA_BATCH_TABLE_SMEM, MUCA_BF16,
+    MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION, MUCA_FP32, MUCA_FP64, MUCA_ISING, MUCA_POTTS, MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL,
     MUCA_STAGING_SHARED,
     MucaConfig, MucaError, MucaIterStats, MucaJob, check, declared_symbols, lib)
 
@@ -259,6 +259,10 @@ class MucaBatch:
         out = np.full(len(self.jobs), -1, dtype=np.int32)
         check(lib().muca_batch_converge(self._h, n_sweeps, therm_sweeps, max_iterations, _ptr(out)))
         return out
+
+    def plan(self, j):
+        """Staging of job j in the persistent kernel (MUCA_BATCH_* bit mask)."""
+        return check(lib().muca_batch_plan(self._h, j))
 
     def autotune(self, n_sweeps, cache_path=None):
         chosen = (ctypes.c_int * 3)()

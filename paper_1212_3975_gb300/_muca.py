@@ -18,6 +18,7 @@ MUCA_FP64, MUCA_FP32, MUCA_BF16 = 0, 1, 2
 MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE = 0, 1
 MUCA_STAGING_AUTO, MUCA_STAGING_SHARED, MUCA_STAGING_GLOBAL = 0, 1, 2
 MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION = 0, 1
+MUCA_BATCH_LATTICE_SMEM, MUCA_BATCH_HIST_SMEM, MUCA_BATCH_TABLE_SMEM, MUCA_BATCH_PAIR_HIST = 1, 2, 4, 8
 
 ERROR_NAMES = {-1: "MUCA_ERR_ARG", -2: "MUCA_ERR_CUDA", -3: "MUCA_ERR_OOM",
                -4: "MUCA_ERR_TIMEOUT", -5: "MUCA_ERR_STATE", -6: "MUCA_ERR_IO"}
@@ -91,6 +92,7 @@ _SIGS = {
     "muca_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "muca_batch_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "muca_batch_job": (_P, [_P, ctypes.c_int]),
+    "muca_batch_plan": (ctypes.c_int, [_P, ctypes.c_int]),
     "muca_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
     "muca_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "muca_load": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_char_p, _P]),

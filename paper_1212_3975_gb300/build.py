@@ -13,7 +13,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 # FP64 update: round every product and sum as written (no FMA contraction)
 EXTRA = {"weights_kernels.cu": ["-fmad=false"]}
-SOURCES = ["muca_api.cu", "sweep_kernels.cu", "sweep_fast.cu", "sweep_ws.cu", "weights_kernels.cu", "reweight_kernels.cu",
+SOURCES = ["muca_api.cu", "sweep_kernels.cu", "sweep_ws.cu", "weights_kernels.cu", "reweight_kernels.cu",
            "reweight_noalloc.cu", "batch.cu", "interface.cu", "muma.cu"]
 
 

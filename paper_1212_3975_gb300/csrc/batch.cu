@@ -92,25 +92,36 @@ __device__ __forceinline__ void run_unit(const SweepArgs &a, int flags, int cblk
 // Persistent sweep kernel of one weight iteration (or part of it); THERM: sweeps of
 // an intermediate thermalisation (no histogram).
 template <bool THERM>
-__global__ void __launch_bounds__(128) batch_sweep_kernel(const BatchJob *jobs, const BatchUnit *units, int n_units,
+__global__ void __launch_bounds__(128, 1) batch_sweep_kernel(const BatchJob *jobs, const BatchUnit *units, int n_units,
                                                           unsigned *queue, int n_sweeps, uint32_t sweep0)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ int s_unit;
+    __shared__ int s_unit, s_model, s_flags, s_cblk;
+    // The unit's arguments live in shared memory and the bodies read them where they
+    // need them (the standalone kernels read theirs from the parameter bank); built in
+    // registers they raised the register pressure of the bodies into spills.
+    __shared__ SweepArgs s_args;
     for (;;) {
+        __syncthreads();  // every warp is done with the previous unit's arguments
+        if (threadIdx.x == 0) {
+            const int u = (int)atomicAdd(queue, 1u);
+            s_unit = u;
+            if (u < n_units) {
+                const BatchUnit un = units[u];
+                const BatchJob &j = jobs[un.job];
+                s_model = *j.active ? j.model : -1;  // -1: converged, frozen
+                s_flags = j.flags;
+                s_cblk = un.cblk;
+                s_args = batch_args(j, n_sweeps, sweep0, THERM);
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 0) s_unit = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int u = s_unit;
-        if (u >= n_units) break;
-        const BatchUnit un = units[u];
-        const BatchJob &j = jobs[un.job];
-        if (!*j.active) continue;  // converged: frozen
-        const SweepArgs a = batch_args(j, n_sweeps, sweep0, THERM);
-        if (j.model == MUCA_ISING)
-            run_unit<MUCA_ISING, !THERM>(a, j.flags, un.cblk, smem);
-        else
-            run_unit<MUCA_POTTS, !THERM>(a, j.flags, un.cblk, smem);
+        if (s_unit >= n_units) break;
+        const int model = s_model;
+        if (model == MUCA_ISING)
+            run_unit<MUCA_ISING, !THERM>(s_args, s_flags, s_cblk, smem);
+        else if (model == MUCA_POTTS)
+            run_unit<MUCA_POTTS, !THERM>(s_args, s_flags, s_cblk, smem);
     }
 }
 
@@ -491,6 +502,12 @@ muca_ctx *muca_batch_job(muca_batch *b, int j)
 {
     if (!b || j < 0 || j >= b->n_jobs) return nullptr;
     return b->ctx[j];
+}
+
+int muca_batch_plan(const muca_batch *b, int j)
+{
+    if (!b || j < 0 || j >= b->n_jobs) return fail(MUCA_ERR_ARG, "no such job");
+    return b->h_jobs[j].flags;
 }
 
 namespace {

@@ -213,6 +213,11 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
     c->cfg = c0;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1) {
+        cudaGetLastError();
+        delete c;
+        return fail(MUCA_ERR_CUDA, "cannot query the multiprocessor count");
+    }
     c->row_words = model == MUCA_ISING ? (L + 31) / 32 : (L + 3) / 4;
     c->lat_words = L * c->row_words;
     c->p_pad = (p + 31) / 32 * 32;

@@ -133,6 +133,7 @@ struct muca_ctx {
     muca_config cfg;
     cudaStream_t stream;
     int device;
+    int n_sm;                 // streaming multiprocessors of the device (queried at init)
     int row_words, lat_words, p_pad;
     // device state
     uint32_t *d_lat;
@@ -198,7 +199,5 @@ int launch_muma_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t swe
                        int32_t *E_rec, int32_t *M_rec);
 cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,
                             cudaStream_t st);
-cudaError_t launch_fast_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist,
-                              bool record, cudaStream_t st);
 
 }  // namespace muca

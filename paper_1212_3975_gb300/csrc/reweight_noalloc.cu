@@ -8,11 +8,14 @@
 // every input and output, and the per-bin scratch of the reweighting kernels lives
 // in one fixed file-scope device array instead of memory owned by a context.
 //
-// The array is part of this library's device image, so every GPU that loads the
-// library holds it (kNoallocMaxBins * 5 doubles, 655,400 bytes) until the process
-// exits.  Host code may not use the array's name as a device address; the address
-// is looked up once per device with cudaGetSymbolAddress.
-#include <atomic>
+// The array is part of this library's device image: once the image is loaded on a
+// GPU (with CUDA's default lazy loading, at the first call on that device, which
+// therefore needs 655,400 bytes of free device memory once; make that first call at
+// start-up, before any stream capture), the GPU holds it (kNoallocMaxBins * 5
+// doubles) until the process exits.  Host code may not use the array's name as a
+// device address; every call looks the address up with cudaGetSymbolAddress for the
+// current device, so a device reset or a newly created primary context (which may
+// place the array elsewhere) never leaves a stale address behind.
 #include <string>
 
 #include "muca_internal.cuh"
@@ -26,23 +29,22 @@ cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, co
 namespace {
 
 constexpr int kNoallocMaxBins = 16385;  // Ising L <= 128, 8-Potts L <= 90
-constexpr int kMaxDevices = 64;
 
 // Per-bin scratch: 5 arrays of kNoallocMaxBins doubles (ln n - ln W, E, mean |M|,
 // mean M^2, within-bin variance of |M|).  Every entry a call reads is written by the
 // same call first, so nothing has to start at zero.
 static __device__ __align__(256) double g_noalloc_scratch[5 * kNoallocMaxBins];
 
-std::atomic<double *> g_scratch_addr[kMaxDevices];
-
-bool device_pointer(const void *p)
+// device (or managed) memory that the current device `dev` can use
+bool device_pointer_on(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -68,20 +70,19 @@ extern "C" int muca_reweight_noalloc(int model, int L, int q, const uint64_t *sa
     if (precision != MUCA_FP64 && precision != MUCA_FP32)
         return fail(MUCA_ERR_ARG, "muca_reweight_noalloc supports MUCA_FP64 and MUCA_FP32");
     if (!samples || !lnw || !betas || !out) return fail(MUCA_ERR_ARG, "null buffer");
-    if (!device_pointer(samples) || !device_pointer(lnw) || !device_pointer(betas) || !device_pointer(out))
-        return fail(MUCA_ERR_ARG, "muca_reweight_noalloc needs device buffers for all inputs and outputs");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return muca::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(MUCA_ERR_ARG, "device index beyond the supported range");
-    double *scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!scratch) {
-        // one-time set-up on this device (the device must be current)
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&scratch), g_noalloc_scratch);
-        if (e != cudaSuccess) return muca::cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-        g_scratch_addr[dev].store(scratch, std::memory_order_release);
-    }
+    if (!device_pointer_on(samples, dev) || !device_pointer_on(lnw, dev) || !device_pointer_on(betas, dev) ||
+        !device_pointer_on(out, dev))
+        return fail(MUCA_ERR_ARG,
+                    "muca_reweight_noalloc needs device buffers of the current device for all inputs and outputs");
+    // the array's address on the current device and context (the first call on a
+    // device loads the library's device image there)
+    double *scratch = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void **>(&scratch), g_noalloc_scratch);
+    if (e != cudaSuccess) return muca::cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
     e = muca::launch_reweight_buffers(scratch, samples, lnw, model, L, q, betas, n_beta, precision, out,
                                       static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return muca::cuda_fail(e, "muca_reweight_noalloc launch");

@@ -445,7 +445,7 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs)
         // Spread the chains over the SMs: one warp per block while that leaves SMs
         // idle, larger blocks once there are more warps than SMs.
         const int warps = ctx->p_pad / 32;
-        cpb = warps <= 152 ? 32 : warps <= 608 ? 64 : 128;
+        cpb = warps <= ctx->n_sm ? 32 : warps <= 4 * ctx->n_sm ? 64 : 128;
     }
     cpb = std::max(32, std::min(256, (cpb / 32) * 32));
     const bool fast = (ctx->L % 4) == 0;
@@ -523,7 +523,6 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
         a.M_rec = M_rec ? M_rec + (size_t)done * ctx->p : nullptr;
         const bool record = E_rec || M_rec || samples;
         cudaError_t e = pl.warp_specialized ? launch_ws_sweep(a, pl, ctx->model, blocks, hist, record, ctx->stream)
-                        : fast ? launch_fast_sweep(a, pl, ctx->model, blocks, hist, record, ctx->stream)
                         : ctx->model == MUCA_ISING ? dispatch_mode<MUCA_ISING>(a, pl, blocks, hist, record, ctx->stream)
                                                    : dispatch_mode<MUCA_POTTS>(a, pl, blocks, hist, record, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
@@ -556,7 +555,7 @@ int launch_recount(muca_ctx *ctx)
 int launch_unpack_spins(muca_ctx *ctx, int8_t *d_out)
 {
     const size_t total = (size_t)ctx->V * ctx->p;
-    const int grid = (int)std::min<size_t>(152 * 16, (total + 255) / 256);
+    const int grid = (int)std::min<size_t>((size_t)ctx->n_sm * 16, (total + 255) / 256);
     unpack_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->d_lat, d_out, ctx->model, ctx->L, ctx->p, ctx->p_pad,
                                                 ctx->row_words);
     MUCA_CUDA_TRY(cudaGetLastError());

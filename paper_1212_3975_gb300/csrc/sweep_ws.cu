@@ -6,7 +6,7 @@ namespace {
 using namespace ws;
 
 template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
-__global__ void __launch_bounds__(128) ising_ws_kernel(SweepArgs a)
+__global__ void __launch_bounds__(128, 1) ising_ws_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     ising_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM>(a, blockIdx.x, smem);

@@ -42,6 +42,27 @@ __global__ void thresholds_kernel(const double *lnw, const uint8_t *acc, uint32_
     thr[t] = A;
 }
 
+// Kernel layout of the thresholds for the warp-specialised sweep bodies: one row per
+// bin, one column per local configuration so that the column offset follows from the
+// neighbours without a branch.  Ising: column = number of unequal neighbours n
+// (dE = 8 - 4n, so n = 2 is dE = 0 and always accepts); Potts: column = dE + 4.
+__global__ void ktab_kernel(const uint32_t *thr, uint32_t *ktab, int model, int n_bins)
+{
+    const int width = model == MUCA_ISING ? 5 : 9;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_bins * width) return;
+    const int b = t / width, k = t % width;
+    uint32_t v;
+    if (model == MUCA_ISING) {
+        // API columns by ascending dE: -8, -4, 4, 8 (n = 4, 3, 1, 0)
+        v = k == 2 ? kAlways : thr[b * 4 + (k >= 3 ? 4 - k : 3 - k)];
+    } else {
+        const int dE = k - 4;
+        v = dE == 0 ? kAlways : thr[b * 8 + (dE < 0 ? dE + 4 : dE + 3)];
+    }
+    ktab[t] = v;
+}
+
 struct BlockStats {
     unsigned long long total, mn, mx, n_sampled, K;
     int lo, hi;
@@ -277,6 +298,17 @@ int launch_update(muca_ctx *ctx)
     MUCA_CUDA_TRY(cudaGetLastError());
     note_launches(1);
     return launch_thresholds(ctx);
+}
+
+int launch_ktab(muca_ctx *ctx)
+{
+    const int width = ctx->model == MUCA_ISING ? 5 : 9;
+    const int n = ctx->n_bins * width;
+    ktab_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_thr, ctx->d_ktab, ctx->model, ctx->n_bins);
+    MUCA_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+    ctx->ktab_dirty = 0;
+    return MUCA_OK;
 }
 
 }  // namespace muca

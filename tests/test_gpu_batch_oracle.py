@@ -1,0 +1,76 @@
+"""Batched form against the CPU oracle on the mixed workload's own job list.
+
+The mixed workload is Ising L = 16, 24, 32, 48, 64, 96, 128 and 8-Potts L = 16, 24,
+32, 48, 256 chains each, in one persistent sweep kernel per weight iteration.  Its job
+list decides the staging of every job (every block gets the shared memory of the
+largest job), so only this list exercises what the batched workload really runs: the
+Ising 96x96 and 128x128 jobs read their threshold tables from global memory, the
+smaller Ising jobs count pairs of attempts where that fits, the others one count per
+attempt.  The batch runs with its autotuned launch shape and as a CUDA graph, one
+weight iteration per call; after each call every job's merged histogram is compared
+bit for bit with the oracle's (all 256 chains, fed the GPU's thresholds of that
+iteration), its ln W after the update within 1e-12 of the oracle's update of the same
+histogram, and every chain's spins, E and M bit for bit (Sec. 2, Parallel Version:
+each chain follows the same Markov chain however the chains are scheduled).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import MucaOracle, weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def muca():
+    import paper_1212_3975_gb300 as m
+    from paper_1212_3975_gb300 import build
+    build.build()
+    return m
+
+
+def lnw_close(a, b, tol=1e-12):
+    scale = np.maximum(1.0, np.maximum(np.abs(a), np.abs(b)))
+    return float(np.max(np.abs(a - b) / scale)) <= tol
+
+
+def test_mixed_batch_matches_oracle(muca, tmp_path):
+    m = muca
+    jobs = workloads.BATCHED_MIXED["jobs"]
+    sweeps, iterations = 10, 2
+    b = m.MucaBatch(jobs)
+    choice = b.autotune(sweeps, str(tmp_path / "tune.json"))
+    assert choice[0] >= 1
+    plans = [b.plan(j) for j in range(len(jobs))]
+    # the paths the mixed workload takes are the ones checked here
+    for j, (model, L, _, _, _) in enumerate(jobs):
+        if model == m.MUCA_ISING and L >= 96:
+            assert not plans[j] & m.MUCA_BATCH_TABLE_SMEM, (L, plans[j])   # global table
+    assert any(plans[j] & m.MUCA_BATCH_PAIR_HIST for j in range(len(jobs))), plans
+    assert any(not plans[j] & m.MUCA_BATCH_PAIR_HIST and plans[j] & m.MUCA_BATCH_HIST_SMEM
+               for j in range(len(jobs))), plans
+
+    oracles = [MucaOracle(model, L, q, p, seed) for (model, L, q, p, seed) in jobs]
+    thr = [b.job(j).get_thresholds() for j in range(len(jobs))]
+    for it in range(iterations):
+        b.iterate(1, sweeps, graph=True)
+        for j, (model, L, q, p, seed) in enumerate(jobs):
+            v, o = b.job(j), oracles[j]
+            H = v.get_histogram()
+            h = o.iterate(sweeps, thr=thr[j])
+            assert int(H.sum()) == p * sweeps * L * L, (j, it)
+            assert np.array_equal(H, h), ("histogram", model, L, it)
+            spins = v.get_spins()
+            E, M = v.get_energies()
+            assert np.array_equal(spins, o.spins), ("spins", model, L, it)
+            assert np.array_equal(E, o.E) and np.array_equal(M, o.M), ("E/M", model, L, it)
+            o.update_weights(h)
+            assert lnw_close(v.get_lnw(), o.lnw), ("ln W", model, L, it)
+            assert v.iteration == it + 1
+            # the next iteration runs with the GPU's table; tables built on each side
+            # from the same ln W differ at most by one in rare knife-edge entries
+            thr[j] = v.get_thresholds()
+            own = weights.thresholds(model, L, o.lnw).astype(np.int64)
+            assert np.abs(thr[j].astype(np.int64) - own).max() <= 1
+    b.close()

@@ -1,6 +1,6 @@
-"""The decider-loop replica (tests/gpu_decider_loop.cu) builds and runs: it gives the
-cycles per attempt of the Ising decider's loop alone on one warp, the C_crit of the
-chain-latency bound that bench.py reports."""
+"""The decider-loop replica (tests/gpu_decider_loop.cu) builds and runs on one warp
+per block and prints the cycles per site of the Ising stream decider's loop alone:
+the C_crit of the chain-latency bound that bench.py reports."""
 import os
 import re
 import shutil
@@ -21,10 +21,9 @@ def test_decider_loop_replica():
         subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
                         os.path.join(HERE, "gpu_decider_loop.cu")], check=True)
         out = subprocess.run([exe], check=True, capture_output=True, text=True, timeout=300).stdout
-    vals = {int(m.group(1)): float(m.group(2)) for m in re.finditer(r"mode (\d+) \(.*?\): ([0-9.]+)", out)}
-    assert set(vals) == set(range(13)), out
-    assert all(2.0 < v < 500.0 for v in vals.values()), out
-    # the accept chain alone is the shortest, the full loop among the longest; the
-    # byte-parallel loop is no slower than the per-site one
-    assert vals[5] < vals[3] < vals[0]
-    assert vals[10] <= vals[0] * 1.02
+    m = re.search(r"decider loop: ([0-9.]+) cycles/site", out)
+    assert m, out
+    print(out.strip())
+    # a site needs at least a dependent select -> compare; far more would mean the
+    # replica no longer runs the loop it stands for
+    assert 5.0 < float(m.group(1)) < 200.0, out

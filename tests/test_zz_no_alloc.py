@@ -39,8 +39,10 @@ def test_noalloc_matches_context_reweight(precision, tol):
     build.build()
     lib = m.lib()
     prec = m.PRECISIONS[precision]
-    cases = [(m.MUCA_ISING, 16, 2, 0.42, 0.30, 0.55, 61), (m.MUCA_POTTS, 12, 8, 1.33, 1.20, 1.40, 37)]
-    for model, L, q, beta, lo, hi, n_beta in cases:          # two calls in a row
+    # two calls in a row, the larger lattice (289 bins) first, so that the second call
+    # (257 bins) would read anything stale the first one left in the shared scratch
+    cases = [(m.MUCA_POTTS, 12, 8, 1.33, 1.20, 1.40, 37), (m.MUCA_ISING, 16, 2, 0.42, 0.30, 0.55, 61)]
+    for model, L, q, beta, lo, hi, n_beta in cases:
         g = _produce(m, model, L, q, beta, seed=11)
         betas = np.linspace(lo, hi, n_beta)
         ref = g.reweight(betas, precision)
@@ -57,6 +59,15 @@ def test_noalloc_matches_context_reweight(precision, tol):
         for row, key in enumerate(("e", "C", "absm", "chi")):
             rel = np.abs(got[row] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
             assert rel.max() <= tol, (model, key, rel.max())
+        # a repeated call takes no device memory (the scratch is already loaded) and
+        # gives the same result
+        out2 = torch.full((4, n_beta), float("nan"), dtype=torch.float64, device="cuda")
+        free1 = torch.cuda.mem_get_info()[0]
+        m.check(lib.muca_reweight_noalloc(model, L, q, _ptr(samples), _ptr(lnw), _ptr(betas_d), n_beta, prec,
+                                          _ptr(out2), None))
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free1, "the allocation-free call changed free device memory"
+        assert torch.equal(out2, out)
         g.close()
 
 
