@@ -523,7 +523,9 @@ def run_probe(args):
     import paper_1212_3975_gb300 as m
     from paper_1212_3975_gb300 import build as b
     b.build()
-    w = workloads.WORKLOADS[args.probe]
+    w = dict(workloads.WORKLOADS[args.probe])
+    if args.probe_p:
+        w["p"] = args.probe_p
     g = m.Muca(w["model"], w["L"], w["q"], w["p"], w["seed"])
     if w.get("fixed_beta"):
         lnw = workloads.canonical_lnw(w["model"], w["L"], w["fixed_beta"])
@@ -535,7 +537,7 @@ def run_probe(args):
     g.iterate(args.probe_sweeps)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    print(json.dumps({"probe": args.probe, "sweeps": args.probe_sweeps,
+    print(json.dumps({"probe": args.probe, "p": w["p"], "plan": g.plan(), "sweeps": args.probe_sweeps,
                       "attempts_per_ns": w["p"] * w["L"] * w["L"] * args.probe_sweeps / dt / 1e9}))
     g.close()
 
@@ -602,6 +604,7 @@ def main():
     ap.add_argument("--probe", default=None, choices=sorted(workloads.WORKLOADS),
                     help="run one small sweep launch of a workload (for profiler captures)")
     ap.add_argument("--probe-sweeps", type=int, default=10)
+    ap.add_argument("--probe-p", type=int, default=0, help="number of chains of the probe (default: the workload's)")
     args = ap.parse_args()
     if args.probe:
         run_probe(args)

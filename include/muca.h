@@ -236,6 +236,24 @@ int muca_get_histogram(muca_ctx *ctx, uint64_t *H);
 int muca_get_samples(muca_ctx *ctx, uint64_t *n, uint64_t *sum_abs_m, uint64_t *sum_m2);
 int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
 
+/* How the sweep kernels stage this context's chains (introspection for tests and
+ * tuning; the choice depends on L, p, the device and cfg->staging): a bit mask of
+ *  MUCA_PLAN_LATTICE_SMEM   lattices in shared memory (else global memory, L1/L2),
+ *  MUCA_PLAN_HIST_SMEM      block histogram in shared memory (else global atomics),
+ *  MUCA_PLAN_TABLE_SMEM     threshold table in shared memory (else global memory),
+ *  MUCA_PLAN_PAIR_HIST      histogram of pairs of consecutive attempts,
+ *  MUCA_PLAN_COMPACT        compact staging, two blocks per SM (more groups of 32
+ *                           chains than SMs),
+ *  MUCA_PLAN_WARP_SPECIALIZED  decider / producer / bookkeeper warps (L % 4 == 0).
+ * Errors: MUCA_ERR_ARG (null context). */
+#define MUCA_PLAN_LATTICE_SMEM 1
+#define MUCA_PLAN_HIST_SMEM 2
+#define MUCA_PLAN_TABLE_SMEM 4
+#define MUCA_PLAN_PAIR_HIST 8
+#define MUCA_PLAN_COMPACT 16
+#define MUCA_PLAN_WARP_SPECIALIZED 32
+int muca_sweep_plan(const muca_ctx *ctx);
+
 /* ---------------------------------------------------------------------------
  * Batched form (not in the paper): many independent lattices -- uneven L, both
  * models -- advance together.  Each lattice is a full context (its own chains,
@@ -283,15 +301,8 @@ int muca_batch_converge(muca_batch *b, int n_sweeps, int therm_sweeps, int max_i
 muca_ctx *muca_batch_job(muca_batch *b, int j);
 
 /* How the persistent sweep kernel stages job j (as configured by muca_batch_create
- * or the last muca_batch_autotune): a bit mask, MUCA_BATCH_PAIR_HIST (histogram of
- * pairs of consecutive attempts), MUCA_BATCH_TABLE_SMEM (threshold table in shared
- * memory; otherwise read from global memory), MUCA_BATCH_HIST_SMEM (block histogram
- * in shared memory), MUCA_BATCH_LATTICE_SMEM (lattices in shared memory).
+ * or the last muca_batch_autotune): a MUCA_PLAN_* bit mask (see muca_sweep_plan).
  * Errors: MUCA_ERR_ARG (no such job). */
-#define MUCA_BATCH_LATTICE_SMEM 1
-#define MUCA_BATCH_HIST_SMEM 2
-#define MUCA_BATCH_TABLE_SMEM 4
-#define MUCA_BATCH_PAIR_HIST 8
 int muca_batch_plan(const muca_batch *b, int j);
 
 /* Pick the persistent grid size, the lattice staging and the number of sweep

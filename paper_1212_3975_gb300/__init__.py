@@ -10,7 +10,8 @@ import ctypes
 import numpy as np
 
 from ._muca import (  # noqa: F401
-    MUCA_BATCH_HIST_SMEM, MUCA_BATCH_LATTICE_SMEM, MUCA_BATCH_PAIR_HIST, MUCA_BATCH_TABLE_SMEM, MUCA_BF16,
+    MUCA_BF16, MUCA_PLAN_COMPACT, MUCA_PLAN_HIST_SMEM, MUCA_PLAN_LATTICE_SMEM, MUCA_PLAN_PAIR_HIST,
+    MUCA_PLAN_TABLE_SMEM, MUCA_PLAN_WARP_SPECIALIZED,
     MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION, MUCA_FP32, MUCA_FP64, MUCA_ISING, MUCA_POTTS, MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL,
     MUCA_STAGING_SHARED,
     MucaConfig, MucaError, MucaIterStats, MucaJob, check, declared_symbols, lib)
@@ -196,6 +197,10 @@ class Muca:
         check(lib().muca_get_samples(self._h, _ptr(n), _ptr(s1), _ptr(s2)))
         return n, s1, s2
 
+    def plan(self):
+        """Staging of the sweep kernels for this context (MUCA_PLAN_* bit mask)."""
+        return check(lib().muca_sweep_plan(self._h))
+
     @property
     def iteration(self):
         return lib().muca_get_iteration(self._h)
@@ -261,7 +266,7 @@ class MucaBatch:
         return out
 
     def plan(self, j):
-        """Staging of job j in the persistent kernel (MUCA_BATCH_* bit mask)."""
+        """Staging of job j in the persistent kernel (MUCA_PLAN_* bit mask)."""
         return check(lib().muca_batch_plan(self._h, j))
 
     def autotune(self, n_sweeps, cache_path=None):

@@ -18,7 +18,8 @@ MUCA_FP64, MUCA_FP32, MUCA_BF16 = 0, 1, 2
 MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE = 0, 1
 MUCA_STAGING_AUTO, MUCA_STAGING_SHARED, MUCA_STAGING_GLOBAL = 0, 1, 2
 MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION = 0, 1
-MUCA_BATCH_LATTICE_SMEM, MUCA_BATCH_HIST_SMEM, MUCA_BATCH_TABLE_SMEM, MUCA_BATCH_PAIR_HIST = 1, 2, 4, 8
+MUCA_PLAN_LATTICE_SMEM, MUCA_PLAN_HIST_SMEM, MUCA_PLAN_TABLE_SMEM, MUCA_PLAN_PAIR_HIST = 1, 2, 4, 8
+MUCA_PLAN_COMPACT, MUCA_PLAN_WARP_SPECIALIZED = 16, 32
 
 ERROR_NAMES = {-1: "MUCA_ERR_ARG", -2: "MUCA_ERR_CUDA", -3: "MUCA_ERR_OOM",
                -4: "MUCA_ERR_TIMEOUT", -5: "MUCA_ERR_STATE", -6: "MUCA_ERR_IO"}
@@ -64,6 +65,7 @@ _SIGS = {
     "muca_n_de": (ctypes.c_int, [_P]),
     "muca_num_chains": (ctypes.c_int, [_P]),
     "muca_get_iteration": (ctypes.c_int, [_P]),
+    "muca_sweep_plan": (ctypes.c_int, [_P]),
     "muca_iterate": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "muca_update_weights": (ctypes.c_int, [_P, ctypes.POINTER(MucaIterStats)]),
     "muca_thermalize": (ctypes.c_int, [_P, ctypes.c_int]),

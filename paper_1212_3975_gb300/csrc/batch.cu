@@ -198,6 +198,7 @@ struct muca_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<BatchJob> h_jobs;
+    std::vector<int> plan_flags;  // MUCA_PLAN_* of every job
     BatchJob *d_jobs = nullptr;
     BatchUnit *d_units = nullptr;
     int n_units = 0;
@@ -237,6 +238,7 @@ int sm_count()
 int configure(muca_batch *b)
 {
     b->h_jobs.assign(b->n_jobs, BatchJob{});
+    b->plan_flags.assign(b->n_jobs, 0);
     b->smem = 0;
     b->max_bins = b->max_thr = b->max_ktab = 0;
     std::vector<std::pair<long long, BatchUnit>> units;
@@ -246,7 +248,7 @@ int configure(muca_batch *b)
     size_t smem_plain = 0;
     for (int i = 0; i < b->n_jobs; ++i) {
         b->ctx[i]->cfg.staging = b->staging;
-        const SweepPlan pl = plan_sweeps(b->ctx[i], false);
+        const SweepPlan pl = plan_sweeps(b->ctx[i], false, false);
         smem_plain = std::max(smem_plain, pl.smem_bytes + ws_extra_smem(b->ctx[i]->model));
     }
     for (int i = 0; i < b->n_jobs; ++i) {
@@ -256,8 +258,8 @@ int configure(muca_batch *b)
             return fail(MUCA_ERR_ARG, "batched lattices need the energy ensemble (job " + std::to_string(i) + ")");
         // pairs of attempts for Ising (its body has a bookkeeper warp here) within the
         // shared memory of the largest job; the batched Potts body counts per attempt
-        SweepPlan pl = plan_sweeps(c, c->model == MUCA_ISING);
-        if (pl.hist_pairs && pl.smem_bytes + ws_extra_smem(c->model) > smem_plain) pl = plan_sweeps(c, false);
+        SweepPlan pl = plan_sweeps(c, c->model == MUCA_ISING, false);
+        if (pl.hist_pairs && pl.smem_bytes + ws_extra_smem(c->model) > smem_plain) pl = plan_sweeps(c, false, false);
         if (!pl.warp_specialized)
             return fail(MUCA_ERR_ARG, "batched lattices need L % 4 == 0 (job " + std::to_string(i) + ")");
         BatchJob &j = b->h_jobs[i];
@@ -293,6 +295,7 @@ int configure(muca_batch *b)
         j.ctr3_therm = ((uint32_t)(c->seed >> 32) << 2) | kPhaseThermalize;
         j.therm = b->d_therm + i;
         j.flags = (pl.hist_pairs ? 8 : 0) | (pl.table_smem ? 4 : 0) | (pl.hist_smem ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
+        b->plan_flags[i] = plan_flags(pl);
         b->smem = std::max(b->smem, pl.smem_bytes + ws_extra_smem(c->model));
         b->max_bins = std::max(b->max_bins, c->n_bins);
         b->max_thr = std::max(b->max_thr, c->n_bins * c->n_de);
@@ -507,7 +510,7 @@ muca_ctx *muca_batch_job(muca_batch *b, int j)
 int muca_batch_plan(const muca_batch *b, int j)
 {
     if (!b || j < 0 || j >= b->n_jobs) return fail(MUCA_ERR_ARG, "no such job");
-    return b->h_jobs[j].flags;
+    return b->plan_flags[j];
 }
 
 namespace {

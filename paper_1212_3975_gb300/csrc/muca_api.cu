@@ -213,10 +213,14 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
     c->cfg = c0;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&c->device);
-    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1) {
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1 ||
+        cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&c->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, c->device) !=
+            cudaSuccess) {
         cudaGetLastError();
         delete c;
-        return fail(MUCA_ERR_CUDA, "cannot query the multiprocessor count");
+        return fail(MUCA_ERR_CUDA, "cannot query the multiprocessor count and shared memory");
     }
     c->row_words = model == MUCA_ISING ? (L + 31) / 32 : (L + 3) / 4;
     c->lat_words = L * c->row_words;
@@ -285,6 +289,11 @@ int muca_n_bins(const muca_ctx *ctx) { return ctx ? ctx->n_bins : fail(MUCA_ERR_
 int muca_n_de(const muca_ctx *ctx) { return ctx ? ctx->n_de : fail(MUCA_ERR_ARG, "null context"); }
 int muca_num_chains(const muca_ctx *ctx) { return ctx ? ctx->p : fail(MUCA_ERR_ARG, "null context"); }
 int muca_get_iteration(const muca_ctx *ctx) { return ctx ? (int)ctx->iteration : fail(MUCA_ERR_ARG, "null context"); }
+int muca_sweep_plan(const muca_ctx *ctx)
+{
+    if (!ctx) return fail(MUCA_ERR_ARG, "null context");
+    return plan_flags(plan_sweeps(ctx));
+}
 
 int muca_iterate(muca_ctx *ctx, int n_sweeps, uint64_t *H_out)
 {

@@ -99,8 +99,9 @@ struct SweepPlan {
     bool table_smem, hist_smem, lattice_smem;
     bool hist_pairs;        // warp-specialised: shared histogram of attempt pairs
     bool warp_specialized;  // decider / producer / bookkeeper warps per 32 chains
+    bool compact;           // warp-specialised Ising: two blocks per SM (3-slot draw ring)
     int chains_per_block;
-    size_t smem_bytes;
+    size_t smem_bytes;      // staging of the plan (table, histogram, lattices)
 };
 
 // Device view of one lattice of a batch (pointers into its context).
@@ -134,6 +135,8 @@ struct muca_ctx {
     cudaStream_t stream;
     int device;
     int n_sm;                 // streaming multiprocessors of the device (queried at init)
+    int smem_per_sm;          // shared memory per SM and reserved per block (bytes, queried)
+    int smem_reserved;
     int row_words, lat_words, p_pad;
     // device state
     uint32_t *d_lat;
@@ -189,10 +192,11 @@ int launch_update(muca_ctx *ctx);
 int launch_stats(muca_ctx *ctx);
 int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision,
                     double *d_out /* [4][n_beta] */);
-SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs = true);
+SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs = true, bool allow_compact = true);
+int plan_flags(const SweepPlan &pl);  // MUCA_PLAN_* bit mask
 cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st);
 int launch_ktab(muca_ctx *ctx);
-size_t ws_extra_smem(int model);
+size_t ws_extra_smem(int model, bool compact = false);
 // multimagnetic Ising ensemble (muma.cu)
 int launch_muma_thresholds(muca_ctx *ctx);
 int launch_muma_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,

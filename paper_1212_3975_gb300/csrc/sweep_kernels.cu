@@ -437,9 +437,10 @@ cudaError_t dispatch_mode(const SweepArgs &a, const SweepPlan &pl, int blocks, b
 
 }  // namespace
 
-SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs)
+SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
 {
     SweepPlan pl;
+    pl.compact = false;
     int cpb = ctx->cfg.chains_per_block;
     if (cpb <= 0) {
         // Spread the chains over the SMs: one warp per block while that leaves SMs
@@ -474,7 +475,32 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs)
     pl.hist_pairs = allow_pairs && ws && pl.table_smem && pl.hist_smem && pl.lattice_smem && used - hist + pairs <= cap;
     if (pl.hist_pairs) used += pairs - hist;
     pl.smem_bytes = used;
+    // More groups of 32 chains than SMs (the throughput regime): a plan whose block
+    // takes more than half of an SM's shared memory runs one block per SM and leaves
+    // the other groups waiting for a second wave.  The compact Ising staging keeps the
+    // table and a histogram of single attempts in shared memory, the lattices in
+    // global memory (L1/L2) and three draw-ring slots, which fits two blocks per SM.
+    const size_t per_sm = (size_t)ctx->smem_per_sm, reserved = (size_t)ctx->smem_reserved;
+    if (allow_compact && ws && ctx->model == MUCA_ISING && staging != MUCA_STAGING_SHARED &&
+        ctx->p_pad / 32 > ctx->n_sm && pl.table_smem) {
+        const size_t full = used + ws_extra_smem(ctx->model);
+        const size_t comp = table + hist + ws_extra_smem(ctx->model, true);
+        if (2 * (full + reserved) > per_sm && 2 * (comp + reserved) <= per_sm) {
+            pl.compact = true;
+            pl.hist_smem = true;
+            pl.lattice_smem = false;
+            pl.hist_pairs = false;
+            pl.smem_bytes = table + hist;
+        }
+    }
     return pl;
+}
+
+int plan_flags(const SweepPlan &pl)
+{
+    return (pl.lattice_smem ? MUCA_PLAN_LATTICE_SMEM : 0) | (pl.hist_smem ? MUCA_PLAN_HIST_SMEM : 0) |
+           (pl.table_smem ? MUCA_PLAN_TABLE_SMEM : 0) | (pl.hist_pairs ? MUCA_PLAN_PAIR_HIST : 0) |
+           (pl.compact ? MUCA_PLAN_COMPACT : 0) | (pl.warp_specialized ? MUCA_PLAN_WARP_SPECIALIZED : 0);
 }
 
 int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,
@@ -488,7 +514,7 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
         int rc = launch_ktab(ctx);
         if (rc) return rc;
     }
-    if (pl.smem_bytes + (pl.warp_specialized ? ws_extra_smem(ctx->model) : 0) > (size_t)kMaxSmem)
+    if (pl.smem_bytes + (pl.warp_specialized ? ws_extra_smem(ctx->model, pl.compact) : 0) > (size_t)kMaxSmem)
         return fail(MUCA_ERR_ARG, "shared-memory staging does not fit: " + std::to_string(pl.smem_bytes) + " bytes");
     SweepArgs a;
     a.lat = ctx->d_lat;

@@ -5,11 +5,11 @@ namespace muca {
 namespace {
 using namespace ws;
 
-template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU>
 __global__ void __launch_bounds__(128, 1) ising_ws_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    ising_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM>(a, blockIdx.x, smem);
+    ising_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM, RU>(a, blockIdx.x, smem);
 }
 
 // iteration and production launches: five warps (decider, 3 producers, bookkeeper)
@@ -22,13 +22,19 @@ __global__ void __launch_bounds__(160) potts_ws_kernel(SweepArgs a)
 
 // HMODE: histogram in global memory (0), shared per attempt (1), shared per pair of
 // attempts (2)
-template <int MODEL, bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
+template <int MODEL, bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU = kRingU>
 cudaError_t launch_ws(const SweepArgs &a, int blocks, size_t smem, cudaStream_t st)
 {
-    auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM>
+    auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM, RU>
                                     : potts_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (RU != kRingU) {
+        // compact staging: the whole carve-out as shared memory, so two blocks fit
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
     }
     kern<<<blocks, (MODEL == MUCA_POTTS && (HIST || RECORD)) ? 160 : 128, smem, st>>>(a);
@@ -41,6 +47,10 @@ cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size
     // pair histogram: planned only with the table and the lattices in shared memory
     if (HIST && pl.hist_smem && pl.hist_pairs)
         return launch_ws<MODEL, HIST, RECORD, true, 2, true>(a, blocks, smem, st);
+    // compact Ising staging (two blocks per SM): table and histogram in shared memory,
+    // lattices in global memory, three draw-ring slots
+    if (MODEL == MUCA_ISING && pl.compact)
+        return launch_ws<MODEL, HIST, RECORD, true, HIST ? 1 : 0, false, kCompactRing>(a, blocks, smem, st);
     const int key = (pl.table_smem ? 4 : 0) | ((HIST && pl.hist_smem) ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
     switch (key) {
     case 0: return launch_ws<MODEL, HIST, RECORD, false, 0, false>(a, blocks, smem, st);
@@ -57,16 +67,17 @@ cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size
 }  // namespace
 
 // shared memory of the warp-specialised kernels beyond the staging of the plan
-size_t ws_extra_smem(int model)
+size_t ws_extra_smem(int model, bool compact)
 {
-    return model == MUCA_ISING ? (size_t)kRingU * 8 * 32 * sizeof(uint4) + (size_t)kRingS * 32 * sizeof(Snap)
+    const int ring = compact ? kCompactRing : kRingU;
+    return model == MUCA_ISING ? (size_t)ring * 8 * 32 * sizeof(uint4) + (size_t)kRingS * 32 * sizeof(Snap)
                                : potts_ws_extra_smem(true);
 }
 
 cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,
                             cudaStream_t st)
 {
-    const size_t smem = pl.smem_bytes + ws_extra_smem(model);
+    const size_t smem = pl.smem_bytes + ws_extra_smem(model, pl.compact);
     if (model == MUCA_ISING) {
         if (hist && record) return ws_staging<MUCA_ISING, true, true>(a, pl, blocks, smem, st);
         if (hist) return ws_staging<MUCA_ISING, true, false>(a, pl, blocks, smem, st);

@@ -33,6 +33,7 @@ namespace ws {
 
 constexpr int kRingU = 4;   // slots of Philox draws (one row word each)
 constexpr int kRingS = 3;   // slots of bookkeeping snapshots
+constexpr int kCompactRing = 3;  // draw-ring slots of the compact Ising staging
 constexpr int kBarFullU = 1, kBarEmptyU = kBarFullU + kRingU;      // ids 1..8
 constexpr int kBarFullS = kBarEmptyU + kRingU, kBarEmptyS = kBarFullS + kRingS;  // ids 9..14
 static_assert(kBarEmptyS + kRingS <= 16, "named barrier ids");
@@ -152,7 +153,10 @@ __device__ __forceinline__ Quad site_quad(const WordCtx &x, int g, bool rowstart
 // spins, so that case keeps the per-word form.)  The site constants come four sites
 // at a time in byte-parallel form, so a site costs four byte extractions, three
 // selects on the previous decision, three adds, the two loads and the compare.
-template <bool BOOK, bool TSMEM, int RU, int RS>
+// CTX: site of the current word at which the next word's neighbour planes are formed
+// from its lattice words (loaded at the start of the current word): early when the
+// lattices are in shared memory, later when they come from L2.
+template <bool BOOK, bool TSMEM, int RU, int RS, int CTX>
 __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t *lp, const size_t ls,
                                                     const uint32_t tab_s, const uint4 *s_ring, Snap *s_snap,
                                                     const int NU, const int lane, const int total, uint32_t &bin20,
@@ -225,7 +229,7 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
                 else
                     q1 = site_quad(nx, 0, w1 == 0);  // site 0 of the next word
             }
-            if (j == 8) nx = word_ctx(R1, U1, D1w, Rn1, lb1);
+            if (j == CTX) nx = word_ctx(R1, U1, D1w, Rn1, lb1);
             if (j == 28 && has_next) {
                 // first draws of the next word
                 bar_sync(kBarFullU + slot1, NU);
@@ -288,7 +292,8 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
 // ends in bin b + d (|d| <= 2), and the histogram is H[b] = sum_d C[b][d + 2] +
 // sum_d C[b - d][d + 2].  Mode 2 halves the shared-memory atomics, which otherwise
 // delay the decider's table loads.
-template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM>
+// RU: slots of the draw ring (4; 3 in the compact staging that fits two blocks per SM)
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU = kRingU>
 __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
     __syncthreads();  // smem may still be read by a previous work unit of this block
@@ -304,12 +309,44 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     const int n_hist = HPAIR ? a.n_bins * 5 : a.n_bins;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) : 0);
-    uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [kRingU][8][32]
-    Snap *s_snap = reinterpret_cast<Snap *>(s_ring + kRingU * 8 * 32);                   // [kRingS][32]
+    static_assert(RU >= 2 && RU <= kRingU, "draw ring slots");
+    uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [RU][8][32]
+    Snap *s_snap = reinterpret_cast<Snap *>(s_ring + RU * 8 * 32);                       // [kRingS][32]
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int c = cblk * 32 + lane;
     const bool active = c < a.p;
+    // Roles: 0 decider, 1..NP producers, NP+1 bookkeeper.  A warp issues on the SM
+    // sub-partition of its warp slot mod 4, and a block's four warps take the four slots
+    // of one aligned group, one per sub-partition.  In the compact staging two blocks
+    // share an SM; there each decider gets the other block's bookkeeper (the warp that
+    // issues least) as its neighbour on the same sub-partition: the block in an even
+    // slot group puts its decider on sub-partition 0 and its bookkeeper on 3, the other
+    // one the other way round, and the producers take 1 and 2 (measured 3% faster than
+    // the slot order at p = 9728, 64 x 64).  With one block per SM the role is the warp
+    // index, read back from shared memory (measured 5% faster at p = 1024 than taking
+    // it from the thread index directly: the compiler lays the role branches out
+    // differently).  If a block's four sub-partitions are not distinct the role is the
+    // warp index.
+    constexpr bool PAIR_ROLES = RU != kRingU;
+    __shared__ int s_sub[4], s_par;
+    if (lane == 0) {
+        uint32_t slot = 0u;
+        if (PAIR_ROLES) asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
+        s_sub[tid >> 5] = PAIR_ROLES ? (int)(slot & 3u) : (tid >> 5);
+        if (tid == 0) s_par = (int)((slot >> 2) & 1u);
+    }
+    __syncthreads();
+    int warp = s_sub[tid >> 5];
+    if (PAIR_ROLES) {
+        if (((1 << s_sub[0]) | (1 << s_sub[1]) | (1 << s_sub[2]) | (1 << s_sub[3])) == 0xF) {
+            const int dsub = s_par ? 3 : 0;  // the decider's sub-partition
+            // role 3: the bookkeeper (the third producer in launches without one)
+            warp = warp == dsub ? 0 : warp == 3 - dsub ? 3 : warp;
+        } else {
+            warp = tid >> 5;
+        }
+    }
 
     if (TSMEM)
         for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
@@ -344,8 +381,8 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
             for (int y = 0; y < L; ++y) {
                 for (int w = 0; w < RW; ++w, ++it) {
                     const int nb = (w == RW - 1) ? last_bits : 32;
-                    const int slot = it % kRingU;
-                    if (it >= kRingU) bar_sync(kBarEmptyU + slot, NU);
+                    const int slot = it % RU;
+                    if (it >= RU) bar_sync(kBarEmptyU + slot, NU);
                     uint4 *dst = s_ring + slot * 8 * 32 + lane;
                     // the word's blocks are independent: unrolled so that their 10-round
                     // dependency chains interleave
@@ -383,7 +420,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         uint32_t d20p = 0u;                     // its change if the previous attempt was accepted
         bool ap = false;                        // previous attempt accepted
         if (last_bits == 32 && RW >= 2) {
-            ising_decide_stream<BOOK, TSMEM, kRingU, kRingS>(a, lp, ls, tab_s, s_ring, s_snap, NU, lane, total, bin20,
+            ising_decide_stream<BOOK, TSMEM, RU, kRingS, LSMEM ? 8 : 20>(a, lp, ls, tab_s, s_ring, s_snap, NU, lane, total, bin20,
                                                              d20p, ap);
         } else {
         int it = 0;
@@ -409,7 +446,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                     uint32_t lo = ua ^ ub ^ tr;
                     uint32_t hi = (ua & ub) | (tr & (ua ^ ub));
                     const uint32_t qw = R ^ ((R << 1) | lbit);
-                    const int slot = it % kRingU;
+                    const int slot = it % RU;
                     bar_sync(kBarFullU + slot, NU);
                     const uint4 *src = s_ring + slot * 8 * 32 + lane;
                     uint32_t Rw = R;
@@ -519,7 +556,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                         }
                         blk = nxt;
                     }
-                    if (it < total - kRingU) bar_arrive(kBarEmptyU + slot, NU);
+                    if (it < total - RU) bar_arrive(kBarEmptyU + slot, NU);
                     LAT(kr + w) = Rw;
                     if (BOOK) {
                         if (lastw) {

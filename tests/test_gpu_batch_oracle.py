@@ -46,9 +46,9 @@ def test_mixed_batch_matches_oracle(muca, tmp_path):
     # the paths the mixed workload takes are the ones checked here
     for j, (model, L, _, _, _) in enumerate(jobs):
         if model == m.MUCA_ISING and L >= 96:
-            assert not plans[j] & m.MUCA_BATCH_TABLE_SMEM, (L, plans[j])   # global table
-    assert any(plans[j] & m.MUCA_BATCH_PAIR_HIST for j in range(len(jobs))), plans
-    assert any(not plans[j] & m.MUCA_BATCH_PAIR_HIST and plans[j] & m.MUCA_BATCH_HIST_SMEM
+            assert not plans[j] & m.MUCA_PLAN_TABLE_SMEM, (L, plans[j])   # global table
+    assert any(plans[j] & m.MUCA_PLAN_PAIR_HIST for j in range(len(jobs))), plans
+    assert any(not plans[j] & m.MUCA_PLAN_PAIR_HIST and plans[j] & m.MUCA_PLAN_HIST_SMEM
                for j in range(len(jobs))), plans
 
     oracles = [MucaOracle(model, L, q, p, seed) for (model, L, q, p, seed) in jobs]

@@ -161,6 +161,47 @@ def test_produce_records_and_samples(muca, model, L, p):
     assert np.array_equal(n, on) and np.array_equal(s1, os1) and np.array_equal(s2, os2)
 
 
+@pytest.mark.parametrize("L", [48, 64])
+def test_compact_staging_bit_exact(muca, L):
+    """More groups of 32 chains than SMs: the compact staging (two blocks per SM, the
+    table and a histogram of single attempts in shared memory, the lattices in global
+    memory, three draw-ring slots), with a ragged last group.  Every chain runs on both
+    sides with the same tables: iteration histograms, spins, E, M, thermalisation,
+    production records and sums bit for bit."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    p = 32 * (n_sm + 2) + 5
+    seed = 4321
+    lnw = random_weights(ISING, L, L + 3, 0.38)
+    thr = weights.thresholds(ISING, L, lnw)
+    with muca.Muca(ISING, L, 2, p, seed) as g:
+        plan = g.plan()
+        assert plan & muca.MUCA_PLAN_COMPACT and plan & muca.MUCA_PLAN_TABLE_SMEM, plan
+        assert not plan & muca.MUCA_PLAN_LATTICE_SMEM and not plan & muca.MUCA_PLAN_PAIR_HIST, plan
+        g.set_thresholds(thr)
+        H1 = g.iterate(2)
+        H2 = g.iterate(1)
+        spins = g.get_spins()
+        E, M = g.get_energies()
+        g.set_lnw(lnw)
+        g.set_thresholds(thr)
+        g.thermalize(1)
+        Er, Mr = g.produce(2)
+        n, s1, s2 = g.get_samples()
+    o = MucaOracle(ISING, L, 2, p, seed)
+    h1 = o.iterate(2, thr=thr)
+    h2 = o.iterate(1, thr=thr)
+    assert int(H1.sum()) == 2 * p * L * L
+    assert np.array_equal(H1, h1) and np.array_equal(H2, h2)
+    assert np.array_equal(spins, o.spins)
+    assert np.array_equal(E, o.E) and np.array_equal(M, o.M)
+    o.thermalize(1, thr=thr)
+    er, mr = o.produce(2, thr=thr)
+    assert np.array_equal(Er, er) and np.array_equal(Mr, mr)
+    on, os1, os2 = reweight.bin_series(ISING, L, er, mr)
+    assert np.array_equal(n, on) and np.array_equal(s1, os1) and np.array_equal(s2, os2)
+
+
 @pytest.mark.parametrize("model,L,p,accumulated", [(ISING, 8, 16, True), (ISING, 8, 16, False),
                                                    (POTTS, 6, 24, True), (ISING, 32, 40, True)])
 def test_update_matches_oracle_given_histogram(muca, model, L, p, accumulated):
