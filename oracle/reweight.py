@@ -10,7 +10,8 @@ Outputs per beta (readings where the paper defines nothing):
   e    = <E> / V
   C    = beta^2 (<E^2> - <E>^2) / V     (computed as a centred second pass)
   absm = <|M|> / Mnorm                  Mnorm = V (Ising), (q - 1) V (Potts)
-  chi  = beta V (<m^2> - <|m|>^2)       m = M / Mnorm
+  chi  = beta V (<m^2> - <|m|>^2)       m = M / Mnorm, the variance of |m| computed as
+                                        a centred second pass, as C
 
 Two forms are given.  ``reweight_series`` is Eq. 2 written out over the records.
 ``reweight_binned`` regroups the same sums by energy bin, using the exact integer sums
@@ -43,12 +44,12 @@ def reweight_series(model, L, q, lnw, E_rec, M_rec, betas):
         Z = w.sum()
         meanE = (w * E).sum() / Z
         var = (w * (E - meanE) ** 2).sum() / Z
-        absm = (w * Mabs).sum() / Z / mn
-        m2 = (w * Mabs * Mabs).sum() / Z / (mn * mn)
+        meanM = (w * Mabs).sum() / Z
+        varM = (w * (Mabs - meanM) ** 2).sum() / Z
         out["e"][j] = meanE / V
         out["C"][j] = beta * beta * var / V
-        out["absm"][j] = absm
-        out["chi"][j] = beta * V * (m2 - absm * absm)
+        out["absm"][j] = meanM / mn
+        out["chi"][j] = beta * V * varM / (mn * mn)
     return out
 
 
@@ -78,7 +79,9 @@ def reweight_binned(model, L, q, lnw, n, s1, s2, betas):
     lnomega = np.log(nk) - np.asarray(lnw, dtype=np.float64)[keep]
     Ek = Eb[keep]
     mabs_mean = np.asarray(s1)[keep].astype(np.float64) / nk
-    m2_mean = np.asarray(s2)[keep].astype(np.float64) / nk
+    # within-bin variance of |M|, (n s2 - s1^2) / n^2, from exact integers
+    vin = np.array([float((int(a) * int(c) - int(b) * int(b))) / float(int(a) * int(a))
+                    for a, b, c in zip(np.asarray(n)[keep], np.asarray(s1)[keep], np.asarray(s2)[keep])])
     mn = m_norm(model, L, q)
     out = {k: np.zeros(len(betas)) for k in ("e", "C", "absm", "chi")}
     for j, beta in enumerate(betas):
@@ -87,12 +90,13 @@ def reweight_binned(model, L, q, lnw, n, s1, s2, betas):
         Z = w.sum()
         meanE = (w * Ek).sum() / Z
         var = (w * (Ek - meanE) ** 2).sum() / Z
-        absm = (w * mabs_mean).sum() / Z / mn
-        m2 = (w * m2_mean).sum() / Z / (mn * mn)
+        meanM = (w * mabs_mean).sum() / Z
+        # <|M|^2> - <|M|>^2 = sum_b w_b (within-bin variance + (bin mean - <|M|>)^2) / Z
+        varM = (w * (vin + (mabs_mean - meanM) ** 2)).sum() / Z
         out["e"][j] = meanE / V
         out["C"][j] = beta * beta * var / V
-        out["absm"][j] = absm
-        out["chi"][j] = beta * V * (m2 - absm * absm)
+        out["absm"][j] = meanM / mn
+        out["chi"][j] = beta * V * varM / (mn * mn)
     return out
 
 
