@@ -178,6 +178,13 @@ int muca_produce(muca_ctx *ctx, int n_sweeps, int32_t *E_out, int32_t *M_out);
 /* Forget the accumulated production sums. */
 int muca_reset_samples(muca_ctx *ctx);
 
+/* Replace the production sums by caller-supplied ones (n, sum |M|, sum M^2 per bin,
+ * [n_bins] uint64 each, host or device; e.g. sums saved from an earlier run or test
+ * inputs) and take the context's current ln W as the weights they were produced with;
+ * muca_reweight and the interface-tension calls then use them, and later production
+ * records add to them.  Errors: MUCA_ERR_ARG, MUCA_ERR_STATE (multimagnetic ensemble). */
+int muca_set_samples(muca_ctx *ctx, const uint64_t *n, const uint64_t *sum_abs_m, const uint64_t *sum_m2);
+
 /* Time-series reweighting of all production records (Eq. 2) to n_beta inverse
  * temperatures betas[] (host or device, FP64).  Per beta it writes
  *   e    = <E>/V,  C = beta^2 (<E^2> - <E>^2)/V  (C_V of Sec. 5),

@@ -140,6 +140,13 @@ class Muca:
     def reset_samples(self):
         check(lib().muca_reset_samples(self._h))
 
+    def set_samples(self, n, sum_abs_m, sum_m2):
+        """Production sums [n_bins] uint64 x 3, taken with the current ln W."""
+        arrs = [np.ascontiguousarray(x, dtype=np.uint64) for x in (n, sum_abs_m, sum_m2)]
+        for x in arrs:
+            assert x.shape == (self.n_bins,)
+        check(lib().muca_set_samples(self._h, *[_ptr(x) for x in arrs]))
+
     def reweight(self, betas, precision="fp64", out=None):
         """Eq. 2 to every beta; returns dict e, C, absm, chi (numpy FP64)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else precision

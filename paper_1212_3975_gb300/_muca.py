@@ -77,6 +77,7 @@ _SIGS = {
                                      ctypes.POINTER(MucaIterStats)]),
     "muca_produce": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "muca_reset_samples": (ctypes.c_int, [_P]),
+    "muca_set_samples": (ctypes.c_int, [_P, _P, _P, _P]),
     "muca_reweight": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "muca_reweight_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                              ctypes.c_int, ctypes.c_int, _P, _P]),

@@ -85,7 +85,7 @@ void free_ctx(muca_ctx *c)
     if (!c) return;
     void *ptrs[] = {c->d_lat, c->d_E, c->d_M, c->d_cnt, c->d_lnw, c->d_P, c->d_lnw_prod, c->d_acc, c->d_thr,
                     c->d_H, c->d_samples, c->d_stats, c->d_series, c->d_rw, c->d_wscratch,
-                    c->d_rwout, c->d_ktab};
+                    c->d_rwout, c->d_ktab, c->d_rwtile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -130,7 +130,9 @@ int alloc_buffers(muca_ctx *c)
     if ((rc = dalloc(&c->d_H, nb, "histogram"))) return rc;
     if ((rc = dalloc(&c->d_samples, 3 * nb, "production sums"))) return rc;
     if ((rc = dalloc(&c->d_stats, 1, "stats"))) return rc;
-    c->rw_bytes = 5 * nb * sizeof(double);
+    // per-bin FP64 arrays (5), a float copy of ln Omega and the sampled range, each part
+    // 256-byte aligned
+    c->rw_bytes = ((5 * nb * sizeof(double) + 255) & ~(size_t)255) + nb * sizeof(float) + 2 * sizeof(int);
     if ((rc = dalloc(reinterpret_cast<uint8_t **>(&c->d_rw), c->rw_bytes, "reweight scratch"))) return rc;
     if (cudaMallocHost(reinterpret_cast<void **>(&c->h_stats), sizeof(muca_iter_stats)) != cudaSuccess) {
         cudaGetLastError();
@@ -367,6 +369,24 @@ int muca_reset_samples(muca_ctx *ctx)
     if ((rc = check_ctx(ctx))) return rc;
     MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_samples, 0, sizeof(uint64_t) * 3 * ctx->n_bins, ctx->stream));
     ctx->samples_active = 0;
+    return MUCA_OK;
+}
+
+int muca_set_samples(muca_ctx *ctx, const uint64_t *n, const uint64_t *sum_abs_m, const uint64_t *sum_m2)
+{
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (ctx->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
+        return fail(MUCA_ERR_STATE, "no energy production sums in the multimagnetic ensemble");
+    if (!n || !sum_abs_m || !sum_m2) return fail(MUCA_ERR_ARG, "null buffer");
+    const size_t bytes = sizeof(uint64_t) * ctx->n_bins;
+    if ((rc = copy_in(ctx, ctx->d_samples, n, bytes))) return rc;
+    if ((rc = copy_in(ctx, ctx->d_samples + ctx->n_bins, sum_abs_m, bytes))) return rc;
+    if ((rc = copy_in(ctx, ctx->d_samples + 2 * (size_t)ctx->n_bins, sum_m2, bytes))) return rc;
+    MUCA_CUDA_TRY(cudaMemcpyAsync(ctx->d_lnw_prod, ctx->d_lnw, sizeof(double) * ctx->n_bins,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->samples_active = 1;
+    ctx->samples_lnw_version = ctx->lnw_version;
     return MUCA_OK;
 }
 

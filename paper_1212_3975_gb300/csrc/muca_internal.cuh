@@ -159,6 +159,8 @@ struct muca_ctx {
     size_t rw_bytes;
     double *d_rwout;
     size_t rwout_cap;         // doubles
+    void *d_rwtile;           // per-call tile scratch of the reweighting (grown on demand)
+    size_t rwtile_bytes;
     // counters and flags
     uint32_t iteration;
     uint32_t sweeps_therm, sweeps_prod;
@@ -196,6 +198,29 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs = true, bool allow_c
 int plan_flags(const SweepPlan &pl);  // MUCA_PLAN_* bit mask
 cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st);
 int launch_ktab(muca_ctx *ctx);
+// Scratch of the tiled reweighting kernels (reweight_kernels.cu): a per-bin part (five
+// FP64 arrays, a float copy of ln Omega, the sampled range) and a per-call part for
+// n_beta betas (tile parameters, shifts, item offsets, partial sums), 256-byte aligned
+// pieces.
+constexpr int kRwTile = 8;          // betas per tile
+constexpr int kRwMaxChunks = 32;    // bin chunks per tile at most
+constexpr size_t kRwTileParamsBytes = 48;
+constexpr size_t rw_align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t rw_bin_part_bytes(size_t nb) { return rw_align256(5 * nb * 8) + rw_align256(nb * 4 + 8); }
+constexpr size_t rw_tile_part_bytes(size_t n_beta)
+{
+    return rw_align256(kRwTileParamsBytes * ((n_beta + kRwTile - 1) / kRwTile)) + rw_align256(8 * n_beta) +
+           rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile + 1)) +
+           8 * ((n_beta + kRwTile - 1) / kRwTile) * kRwMaxChunks * kRwTile * 6;
+}
+// allocation-free reweighting (reweight_noalloc.cu): the bins and betas per pass it
+// serves, its fixed scratch and the launch on caller buffers
+constexpr int kNoallocMaxBins = 16385;       // Ising L <= 128, 8-Potts L <= 90
+constexpr int kNoallocBetasPerPass = 512;
+constexpr size_t kNoallocScratchBytes = rw_bin_part_bytes(kNoallocMaxBins) + rw_tile_part_bytes(kNoallocBetasPerPass);
+cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, const double *lnw, int model, int L,
+                                    int q, const double *d_betas, int n_beta, int precision, double *d_out, int n_sm,
+                                    cudaStream_t st);
 size_t ws_extra_smem(int model, bool compact = false);
 // multimagnetic Ising ensemble (muma.cu)
 int launch_muma_thresholds(muca_ctx *ctx);

@@ -10,30 +10,28 @@
 //
 // The array is part of this library's device image: once the image is loaded on a
 // GPU (with CUDA's default lazy loading, at the first call on that device, which
-// therefore needs 655,400 bytes of free device memory once; make that first call at
-// start-up, before any stream capture), the GPU holds it (kNoallocMaxBins * 5
-// doubles) until the process exits.  Host code may not use the array's name as a
-// device address; every call looks the address up with cudaGetSymbolAddress for the
-// current device, so a device reset or a newly created primary context (which may
-// place the array elsewhere) never leaves a stale address behind.
+// therefore needs kNoallocScratchBytes = 1,515,520 bytes of free device memory once;
+// make that first call at start-up, before any stream capture), the GPU holds it until
+// the process exits.  Host code may not use the array's name as a device address;
+// every call looks the address up with cudaGetSymbolAddress for the current device, so
+// a device reset or a newly created primary context (which may place the array
+// elsewhere) never leaves a stale address behind.
 #include <string>
 
 #include "muca_internal.cuh"
 
-namespace muca {
-cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, const double *lnw, int model, int L,
-                                    int q, const double *d_betas, int n_beta, int precision, double *d_out,
-                                    cudaStream_t st);
-}
-
 namespace {
 
-constexpr int kNoallocMaxBins = 16385;  // Ising L <= 128, 8-Potts L <= 90
+using muca::kNoallocMaxBins;
 
-// Per-bin scratch: 5 arrays of kNoallocMaxBins doubles (ln n - ln W, E, mean |M|,
-// mean M^2, within-bin variance of |M|).  Every entry a call reads is written by the
-// same call first, so nothing has to start at zero.
-static __device__ __align__(256) double g_noalloc_scratch[5 * kNoallocMaxBins];
+// Scratch of the tiled reweighting kernels for at most kNoallocMaxBins bins and
+// kNoallocBetasPerPass betas per pass: per-bin arrays (ln n - ln W, E, mean |M|, mean
+// M^2, within-bin variance of |M|, a float copy of the first, the sampled range) and
+// per-pass tile parameters, shifts and partial sums.  Every entry a call reads is
+// written by the same call first (the sampled range is reset by each call), so
+// nothing has to start at zero.
+static __device__ __align__(256) double g_noalloc_scratch[muca::kNoallocScratchBytes / sizeof(double)];
+static_assert(muca::kNoallocScratchBytes % sizeof(double) == 0, "scratch size");
 
 // device (or managed) memory that the current device `dev` can use
 bool device_pointer_on(const void *p, int dev)
@@ -83,7 +81,10 @@ extern "C" int muca_reweight_noalloc(int model, int L, int q, const uint64_t *sa
     double *scratch = nullptr;
     e = cudaGetSymbolAddress(reinterpret_cast<void **>(&scratch), g_noalloc_scratch);
     if (e != cudaSuccess) return muca::cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-    e = muca::launch_reweight_buffers(scratch, samples, lnw, model, L, q, betas, n_beta, precision, out,
+    int n_sm = 0;
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return muca::cuda_fail(e, "cudaDeviceGetAttribute");
+    e = muca::launch_reweight_buffers(scratch, samples, lnw, model, L, q, betas, n_beta, precision, out, n_sm,
                                       static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return muca::cuda_fail(e, "muca_reweight_noalloc launch");
     return MUCA_OK;
