@@ -12,8 +12,15 @@ histogram merge, recursion + boundary correction, thresholds), a production run 
 host cores, each step a bounded sample of the same workload.  Under torchrun with
 N > 1 each rank runs an independent replica (its own seed): weak scaling, no
 collective on the data path.
+
+The JSON line carries, besides the contract keys: `roofline` of the dominant kernel
+(the weight-iteration sweeps) with the p-sweep of the same kernel, `cpu_baseline`,
+`reweight` (the bench workload's reweighting rates and errors), `other_workloads`
+(8-Potts 32x32 and the large lattices), `batched`, `statistical_study`,
+`interface_tension`, and last a short `summary` of the headline figures.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -38,6 +45,45 @@ REASON_BITS = {
     0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
     0x100: "display_clock_setting",
 }
+
+# Counters of the sweep kernels measured with ncu (summaries in profiles/), each with
+# the hash of the kernel sources it was measured on; a counter whose hash differs from
+# the current sources is reported as stale (and the fractions built on it as null).
+SWEEP_SOURCES = ["paper_1212_3975_gb300/csrc/ws_bodies.cuh", "paper_1212_3975_gb300/csrc/sweep_ws.cu",
+                 "paper_1212_3975_gb300/csrc/sweep_kernels.cu"]
+COUNTERS = {
+    # Ising 64x64, one block per SM (p = 1024): profiles/ising_ws_sweep_L64_p1024.md
+    "ising_L64": {"source": "211dbf7fb5743202", "inst_per_attempt": 1.869,
+                  "shared_wavefronts_per_attempt": 0.354, "traffic_bytes_per_launch": 681472},
+    # Ising 64x64, compact staging, two blocks per SM (p = 9728):
+    # profiles/ising_ws_compact_L64_p9728.md
+    "ising_L64_compact": {"source": "211dbf7fb5743202", "inst_per_attempt": 1.956,
+                          "shared_wavefronts_per_attempt": 0.381, "traffic_bytes_per_launch": 5170},
+    # 8-Potts 32x32 (p = 4096): profiles/potts_ws_sweep_L32_p4096.md
+    "potts_L32": {"source": "earlier", "inst_per_attempt": 3.44, "shared_wavefronts_per_attempt": 0.52,
+                  "traffic_bytes_per_launch": 4320000},
+}
+# cycles per site of the Ising stream decider's loop run alone on one warp
+# (tests/gpu_decider_loop.cu, profiles/ising_decider_loop_replica.md)
+DECIDER_CYCLES_PER_ATTEMPT_ALONE = 36.6
+# MUFU ex2 results per clock per SM (the special-function units: 4 per sub-partition
+# per clock); the FP32 reweighting evaluates one ex2 per contributing (beta, bin)
+MUFU_EX2_PER_CLK_PER_SM = 16
+
+
+def sweep_source_sha16():
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def counters(name):
+    """The counters of one kernel configuration and whether they match the sources."""
+    c = dict(COUNTERS[name])
+    c["matches_source"] = c["source"] == sweep_source_sha16()
+    return c
 
 
 def dist_info():
@@ -66,6 +112,16 @@ def max_over_ranks(values, world, device):
 def whole_job_rate(attempts_per_rank, world, seconds):
     """Attempts per nanosecond of the whole job: every rank ran its own replica."""
     return attempts_per_rank * world / (seconds * 1e9)
+
+
+def rnd(x, n=4):
+    """Round for the JSON line (None and non-finite values pass as None)."""
+    if x is None:
+        return None
+    x = float(x)
+    if not math.isfinite(x):
+        return None
+    return float("%.*g" % (n, x))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -122,6 +178,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cuda_timer(torch, stream):
+    """Device time (s) of fn() on `stream` by CUDA events, synchronised on both sides."""
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+    return timed
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -134,6 +204,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     b.build()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     w = workloads.WORKLOADS[WORKLOAD]
     stream = torch.cuda.Stream()
     seed0 = w["seed"] + (rank << 20)
@@ -189,13 +260,14 @@ def run_gpu(args):
         elapsed_ms = t0.elapsed_time(t1)
         sweep_ms = [a.elapsed_time(z) for a, z in sweep_events]
 
-    # end to end: host buffers through the C ABI (pinned), copies inside the timing
+    # end to end through the C ABI with pinned host buffers: the betas go in, every
+    # iteration's histogram, all (E, M) records and the observables come out; the same
+    # steps and the same L2 flush as the device-timed value
     E_h = torch.empty((w["production"], w["p"]), dtype=torch.int32, pin_memory=True)
     M_h = torch.empty((w["production"], w["p"]), dtype=torch.int32, pin_memory=True)
     H_h = torch.empty(g.n_bins, dtype=torch.int64, pin_memory=True)
     betas_pin = torch.tensor(betas_h, dtype=torch.float64).pin_memory()
     obs_h = torch.empty((4, n_beta), dtype=torch.float64, pin_memory=True)
-    e2e_steps = max(1, min(args.steps, 3))
 
     def step_host(seed):
         g.reset(seed)
@@ -211,7 +283,8 @@ def run_gpu(args):
         step_host(seed0 + 5000)
         barrier()
         h0 = time.perf_counter()
-        for i in range(e2e_steps):
+        for i in range(args.steps):
+            flush.zero_()
             step_host(seed0 + 6000 + i)
         barrier()
         e2e_s = time.perf_counter() - h0
@@ -219,44 +292,12 @@ def run_gpu(args):
     total_ms, e2e_s = max_over_ranks([elapsed_ms, e2e_s], world, "cuda")
     attempts = workload_attempts(w)
     value = whole_job_rate(attempts * args.steps, world, total_ms * 1e-3)
-    e2e_value = whole_job_rate(attempts * e2e_steps, world, e2e_s)
+    e2e_value = whole_job_rate(attempts * args.steps, world, e2e_s)
 
-    # roofline of the dominant kernel (sweeps of the weight iterations)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    sweep_avg_ms = float(np.mean(sweep_ms))
-    att_per_launch = w["p"] * w["L"] * w["L"] * w["sweeps"]
-    inst_per_attempt = INST_PER_ATTEMPT_ISING_L64
-    achieved = inst_per_attempt * att_per_launch / (sweep_avg_ms * 1e-3) / 1e9   # Gwarp-inst/s
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 4 * sm_max * 1e6 / 1e9
-    # the launch has p/32 blocks of 4 warps, one warp per scheduler it occupies
-    occupied = min(608, (w["p"] + 31) // 32 * 4)
-    roofline = {
-        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-        "frac": achieved / peak,
-        "traffic": TRAFFIC_BYTES_PER_LAUNCH_ISING_L64,
-        "kernel": "ising_ws_kernel (weight-iteration sweeps, warp-specialised)",
-        "launch_ms": sweep_avg_ms,
-        "attempts_per_ns": att_per_launch / (sweep_avg_ms * 1e6),
-        "warp_inst_per_attempt": inst_per_attempt,
-        "peak_note": "152 SMs x 4 schedulers x 1 warp-instruction/clock at %.0f MHz, of measured "
-                     "max clock" % sm_max,
-        "occupied_schedulers": occupied,
-        "frac_of_occupied_schedulers": achieved / (peak * occupied / 608.0),
-        # the three bounds on attempts/ns of the sweeps (all at the measured max clock):
-        # issue (every scheduler busy at this instruction count), shared-memory LSU (one
-        # wavefront per clock per SM at this wavefront count) and chain latency (p chains,
-        # each at the cycles per attempt of the decider's site loop measured alone on
-        # one warp)
-        "bounds_attempts_per_ns": {
-            "issue": 152 * 4 * sm_max * 1e6 / inst_per_attempt / 1e9,
-            "lsu": 152 * sm_max * 1e6 / SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 / 1e9,
-            "latency": w["p"] * sm_max * 1e6 / DECIDER_CYCLES_PER_ATTEMPT_ALONE / 1e9,
-        },
-        "frac_of_latency_bound": (att_per_launch / (sweep_avg_ms * 1e6))
-        / (w["p"] * sm_max * 1e6 / DECIDER_CYCLES_PER_ATTEMPT_ALONE / 1e9),
-    }
+    roofline = sweep_roofline(w, float(np.mean(sweep_ms)), n_sm, sm_max)
     result = {
         "metric": METRIC, "value": value, "unit": "attempts/ns", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -273,23 +314,30 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(w["iterations"] * g.n_bins * 8
                                           + 2 * w["production"] * w["p"] * 4
                                           + 4 * n_beta * 8),
-                "steps": e2e_steps},
+                "steps": args.steps, "l2": "flushed between steps"},
         "gpu_launches": int(launches),
-        "roofline": roofline,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_sample(w, seconds_hint=True)
+    summary = {"value": rnd(value), "e2e": rnd(e2e_value),
+               "sweep_attempts_per_ns": rnd(roofline["attempts_per_ns"]), "sweep_issue_frac": rnd(roofline["frac"], 3)}
     if rank == 0 and not args.no_extras:
         with torch.cuda.stream(stream):
-            result["reweight"] = reweight_rates(m, g, torch, stream, betas_h, betas_d)
+            roofline["p_sweep"] = p_sweep(m, torch, stream, n_sm, sm_max)
+    result["roofline"] = roofline
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0 and not args.no_extras:
+        with torch.cuda.stream(stream):
+            result["reweight"] = reweight_rates(m, torch, stream, n_sm, sm_max, g, betas_h, betas_d)
         g.close()
+        result["other_workloads"] = other_workloads(m, torch, stream, n_sm, sm_max)
         result["batched"] = batched_comparison(m, torch)
-        result["other_workloads"] = other_workloads(m, torch, stream)
         result["statistical_study"] = statistical_study()
         result["interface_tension"] = interface_tension()
+        summary.update(make_summary(result))
     else:
         g.close()
+    result["summary"] = summary
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -297,44 +345,124 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def reweight_rates(m, g, torch, stream, betas_h, betas_d):
-    """Reweighted betas per second of muca_reweight in FP64 and FP32 on the
-    production sums of the last step, and the FP32 error per observable."""
-    n_beta = len(betas_h)
-    out = {}
-    res = {}
-    for name, prec in (("fp64", m.MUCA_FP64), ("fp32", m.MUCA_FP32), ("bf16", m.MUCA_BF16)):
-        o = torch.empty((4, n_beta), dtype=torch.float64, device="cuda")
-        g.reweight(betas_d, prec, out=o)          # warm-up
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        reps = 20
-        e0.record(stream)
-        for _ in range(reps):
-            g.reweight(betas_d, prec, out=o)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        out[name + "_betas_per_s"] = n_beta / (ms * 1e-3)
-        out[name + "_ms"] = ms
-        res[name] = o.cpu().numpy()
-    for name in ("fp32", "bf16"):
-        err = np.abs(res[name] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
-        out[name + "_max_rel_err"] = {k: float(err[i].max()) for i, k in enumerate(("e", "C", "absm", "chi"))}
-        out[name + "_within_1e-6"] = bool(err.max() <= 1e-6)
-    out["n_beta"] = n_beta
-    out["n_bins"] = g.n_bins
+def sweep_roofline(w, sweep_avg_ms, n_sm, sm_max):
+    """Issue roofline of the weight-iteration sweeps of the bench workload."""
+    c = counters("ising_L64")
+    att_per_launch = w["p"] * w["L"] * w["L"] * w["sweeps"]
+    rate = att_per_launch / (sweep_avg_ms * 1e6)           # attempts/ns
+    peak = n_sm * 4 * sm_max * 1e6 / 1e9                   # Gwarp-inst/s
+    inst = c["inst_per_attempt"]
+    achieved = inst * rate                                   # Gwarp-inst/s
+    ok = c["matches_source"]
+    blocks = (w["p"] + 31) // 32
+    occupied = min(4 * n_sm, 4 * blocks)
+    latency = w["p"] * sm_max * 1e6 / DECIDER_CYCLES_PER_ATTEMPT_ALONE / 1e9
+    return {
+        "bound": "alu", "achieved": achieved if ok else None, "peak": peak, "unit": "Gwarp-inst/s",
+        "frac": achieved / peak if ok else None,
+        "traffic": c["traffic_bytes_per_launch"] if ok else None,
+        "kernel": "ising_ws_kernel (weight-iteration sweeps, warp-specialised)",
+        "launch_ms": sweep_avg_ms, "attempts_per_ns": rate,
+        "warp_inst_per_attempt": inst, "counters_match_source": ok,
+        "peak_note": "%d SMs x 4 schedulers x 1 warp-instruction/clock at %.0f MHz, of measured max clock"
+                     % (n_sm, sm_max),
+        "occupied_schedulers": occupied,
+        "frac_of_occupied_schedulers": achieved / (peak * occupied / (4 * n_sm)) if ok else None,
+        # the three bounds on attempts/ns of the sweeps at the measured max clock: issue
+        # (every scheduler busy at this instruction count), shared-memory LSU (one
+        # wavefront per clock per SM) and chain latency (p chains at the decider loop's
+        # cycles per attempt)
+        "bounds_attempts_per_ns": {
+            "issue": 4 * n_sm * sm_max * 1e6 / inst / 1e9,
+            "lsu": n_sm * sm_max * 1e6 / c["shared_wavefronts_per_attempt"] / 1e9,
+            "latency": latency,
+        },
+        "frac_of_latency_bound": rate / latency,
+    }
+
+
+def p_sweep(m, torch, stream, n_sm, sm_max, sweeps=100):
+    """Ising 64x64 weight-iteration launches at growing p: where the issue roofline
+    saturates.  One block of 32 chains per SM up to p = 32 x SMs; beyond, the compact
+    staging runs two blocks per SM."""
+    timed = cuda_timer(torch, stream)
+    peak = n_sm * 4 * sm_max * 1e6 / 1e9
+    out = []
+    for p in (1024, 2048, 32 * n_sm, 64 * n_sm, 128 * n_sm):
+        g = m.Muca(m.MUCA_ISING, 64, 2, p, 1, stream=stream.cuda_stream)
+        g.iterate(2)
+        g.update_weights()
+        g.iterate(10)
+        g.update_weights()
+        plan = g.plan()
+        t = min(timed(lambda: m.check(m.lib().muca_iterate(g.handle, sweeps, None))) for _ in range(2))
+        g.close()
+        rate = p * 4096 * sweeps / t / 1e9
+        c = counters("ising_L64_compact" if plan & m.MUCA_PLAN_COMPACT else "ising_L64")
+        ok = c["matches_source"]
+        out.append({"p": p, "attempts_per_ns": rnd(rate), "compact": bool(plan & m.MUCA_PLAN_COMPACT),
+                    "issue_frac": rnd(rate * c["inst_per_attempt"] / peak, 3) if ok else None,
+                    "lsu_frac": rnd(rate * c["shared_wavefronts_per_attempt"] / (n_sm * sm_max * 1e-3), 3)
+                    if ok else None,
+                    "latency_frac": rnd(rate / (p * sm_max * 1e-3 / DECIDER_CYCLES_PER_ATTEMPT_ALONE), 3)})
     return out
 
 
-def other_workloads(m, torch, stream):
+def reweight_rates(m, torch, stream, n_sm, sm_max, g, betas_h, betas_d):
+    """Reweighting of the bench workload's production sums (the last step's) to its 512
+    betas: betas/s of muca_reweight per precision, the error of FP32 and BF16 against
+    FP64 per observable, and the roofline of the FP32 form (one MUFU ex2 per (beta,
+    bin) whose weight reaches e^-100 of the largest)."""
+    timed = cuda_timer(torch, stream)
+    n_beta = len(betas_h)
+    out = {"workload": WORKLOAD, "n_beta": n_beta, "n_bins": g.n_bins}
+    res = {}
+    for name, prec in (("fp64", m.MUCA_FP64), ("fp32", m.MUCA_FP32), ("bf16", m.MUCA_BF16)):
+        o = torch.empty((4, n_beta), dtype=torch.float64, device="cuda")
+        g.reweight(betas_d, prec, out=o)          # warm-up (and scratch)
+        reps = 20
+        t = timed(lambda: [g.reweight(betas_d, prec, out=o) for _ in range(reps)]) / reps
+        out[name + "_betas_per_s"] = rnd(n_beta / t)
+        out[name + "_us"] = rnd(t * 1e6)
+        res[name] = o.cpu().numpy()
+    for name in ("fp32", "bf16"):
+        err = np.abs(res[name] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
+        out[name + "_max_rel_err"] = {k: rnd(err[i].max(), 3) for i, k in enumerate(("e", "C", "absm", "chi"))}
+        out[name + "_within_1e-6"] = bool(err.max() <= 1e-6)
+    n, _, _ = g.get_samples()
+    exps = contributing_terms(g.model, g.L, n, g.get_lnw(), betas_h)  # weights unchanged since production
+    t32 = out["fp32_us"] * 1e-6
+    peak = n_sm * MUFU_EX2_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    out["roofline_fp32"] = {"bound": "alu", "unit": "Tex2/s", "exps_per_call": exps,
+                            "achieved": rnd(exps / t32 / 1e12), "peak": rnd(peak),
+                            "frac": rnd(exps / t32 / 1e12 / peak, 3),
+                            "peak_note": "%d SMs x %d MUFU ex2/clock at %.0f MHz"
+                                         % (n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_max)}
+    return out
+
+
+def contributing_terms(model, L, n, lnw, betas):
+    """(beta, bin) pairs whose weight reaches e^-100 of the largest at that beta."""
+    V = L * L
+    b = np.nonzero(n)[0]
+    E = 4.0 * b - 2.0 * V if model == 0 else b - 2.0 * V
+    lo = np.log(n[b].astype(np.float64)) - lnw[b]
+    total = 0
+    for beta in betas:
+        a = lo - beta * E
+        total += int(np.count_nonzero(a >= a.max() - 100.0))
+    return total
+
+
+def other_workloads(m, torch, stream, n_sm, sm_max):
     """Rates of the other configurations on a bounded part of their schedules (each line
     says which): 8-Potts 32x32 (one 500-sweep weight iteration from ln W = 0, then
     2000 production sweeps at the fixed canonical weights of beta_0 after 200
     thermalisation sweeps, reweighted to its 1024 betas) and the large lattices at
     fixed ln W = -beta_0 E (100 production sweeps, 4096 betas).  Device time by CUDA
     events on the context's stream; FP32 and BF16 reweighting errors against FP64."""
+    timed = cuda_timer(torch, stream)
+    peak = n_sm * 4 * sm_max * 1e6 / 1e9
     out = {}
     cases = (("potts8_L32_p4096", 500, 2000), ("ising_L256_p8192", 0, 100), ("potts8_L128_p4096", 0, 100))
     for name, it_sweeps, prod in cases:
@@ -343,30 +471,27 @@ def other_workloads(m, torch, stream):
         V = w["L"] * w["L"]
         rec = {"sample": "%s%d production sweeps, %d betas"
                % ("one %d-sweep iteration, " % it_sweeps if it_sweeps else "", prod, w["betas"][2])}
-
-        def timed(fn):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1) * 1e-3
-
         with torch.cuda.stream(stream):
             if it_sweeps:
                 g.iterate(2)
                 g.update_weights()
                 t = timed(lambda: m.check(m.lib().muca_iterate(g.handle, it_sweeps, None)))
-                rec["iterate_attempts_per_ns"] = w["p"] * V * it_sweeps / t / 1e9
+                rate = w["p"] * V * it_sweeps / t / 1e9
+                rec["iterate_attempts_per_ns"] = rnd(rate)
+                c = counters("potts_L32")
+                rec["roofline"] = {"bound": "alu", "unit": "Gwarp-inst/s",
+                                   "warp_inst_per_attempt": c["inst_per_attempt"],
+                                   "frac": rnd(rate * c["inst_per_attempt"] / peak, 3) if c["matches_source"]
+                                   else None,
+                                   "counters_match_source": c["matches_source"],
+                                   "occupied_sms": min(n_sm, w["p"] // 32)}
             beta0 = workloads.ISING_BETA0 if w["model"] == workloads.ISING else workloads.POTTS8_BETA0
             lnw = workloads.canonical_lnw(w["model"], w["L"], w.get("fixed_beta", beta0))
             g.set_lnw(lnw - lnw.max())
             g.thermalize(200 if it_sweeps else 20)
             g.reset_samples()
             t = timed(lambda: m.check(m.lib().muca_produce(g.handle, prod, None, None)))
-            rec["produce_attempts_per_ns"] = w["p"] * V * prod / t / 1e9
+            rec["produce_attempts_per_ns"] = rnd(w["p"] * V * prod / t / 1e9)
             betas_h = workloads.beta_grid(w["betas"])
             betas_d = torch.tensor(betas_h, dtype=torch.float64, device="cuda")
             n_beta = len(betas_h)
@@ -376,11 +501,11 @@ def other_workloads(m, torch, stream):
                 g.reweight(betas_d, prec, out=o)
                 reps = 5
                 t = timed(lambda: [g.reweight(betas_d, prec, out=o) for _ in range(reps)]) / reps
-                rec[prec_name + "_betas_per_s"] = n_beta / t
+                rec[prec_name + "_betas_per_s"] = rnd(n_beta / t)
                 res[prec_name] = o.cpu().numpy()
             for prec_name in ("fp32", "bf16"):
                 err = np.abs(res[prec_name] - res["fp64"]) / np.maximum(np.abs(res["fp64"]), 1e-300)
-                rec[prec_name + "_max_rel_err"] = float(err.max())
+                rec[prec_name + "_max_rel_err"] = rnd(err.max(), 3)
                 rec[prec_name + "_within_1e-6"] = bool(err.max() <= 1e-6)
         g.close()
         out[name] = rec
@@ -495,24 +620,40 @@ def batched_comparison(m, torch):
     b.close()
     return {"workload": "mixed: Ising L=16..128 + 8-Potts L=16..48, 256 chains each, %d x %d sweeps"
                         % (iters, sweeps),
-            "per_lattice_attempts_per_ns": att / t_seq / 1e9,
-            "batched_attempts_per_ns": att / t_bat / 1e9,
-            "speedup": t_seq / t_bat, "per_lattice_s": t_seq, "batched_s": t_bat,
+            "per_lattice_attempts_per_ns": rnd(att / t_seq / 1e9),
+            "batched_attempts_per_ns": rnd(att / t_bat / 1e9),
+            "speedup": rnd(t_seq / t_bat), "per_lattice_s": rnd(t_seq), "batched_s": rnd(t_bat),
             "autotuned": {"grid": choice[0], "staging": choice[1], "launches_per_iteration": choice[2]}}
 
 
-# measured with ncu (inst_executed / attempts) on the weight-iteration sweep kernel of
-# the 64x64 Ising workload; see profiles/
-INST_PER_ATTEMPT_ISING_L64 = 1.89
-# dram__bytes_read.sum + dram__bytes_write.sum of one weight-iteration launch of the same
-# kernel (staging of table, histogram and lattices only; independent of the sweep count)
-TRAFFIC_BYTES_PER_LAUNCH_ISING_L64 = 682240
-# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / attempts of the same capture
-SHARED_WAVEFRONTS_PER_ATTEMPT_ISING_L64 = 0.354
-# cycles per site of the decider's 32-site loop run alone on one warp (a replica of the
-# loop with the same table, draws, byte-parallel site constants and dependency
-# structure, clock64-timed on a GB300)
-DECIDER_CYCLES_PER_ATTEMPT_ALONE = 36.6
+def make_summary(r):
+    """The headline figures of the extras, short enough to stay at the end of the line."""
+    s = {}
+    ps = r["roofline"].get("p_sweep") or []
+    if ps:
+        best = max(ps, key=lambda x: x["attempts_per_ns"] or 0)
+        s["p_sweep_best"] = {k: best[k] for k in ("p", "attempts_per_ns", "issue_frac")}
+    rw = r.get("reweight", {})
+    s["reweight_c2_betas_per_s"] = {k: rw.get(k + "_betas_per_s") for k in ("fp64", "fp32", "bf16")}
+    s["reweight_c2_within_1e-6"] = {k: rw.get(k + "_within_1e-6") for k in ("fp32", "bf16")}
+    s["reweight_c2_fp32_ex2_frac"] = rw.get("roofline_fp32", {}).get("frac")
+    ow = r.get("other_workloads", {})
+    c3 = ow.get("potts8_L32_p4096", {})
+    s["c3_iterate_attempts_per_ns"] = c3.get("iterate_attempts_per_ns")
+    s["c3_issue_frac"] = c3.get("roofline", {}).get("frac")
+    s["c3_reweight_betas_per_s"] = {k: c3.get(k + "_betas_per_s") for k in ("fp64", "fp32", "bf16")}
+    for name in ("ising_L256_p8192", "potts8_L128_p4096"):
+        c5 = ow.get(name, {})
+        key = "c5_" + name.split("_")[0]
+        s[key + "_produce_attempts_per_ns"] = c5.get("produce_attempts_per_ns")
+        s[key + "_fp32_max_rel_err"] = c5.get("fp32_max_rel_err")
+    bt = r.get("batched", {})
+    s["batched_speedup"] = bt.get("speedup")
+    s["batched_attempts_per_ns"] = bt.get("batched_attempts_per_ns")
+    cb = r.get("cpu_baseline", {})
+    if cb:
+        s["cpu_attempts_per_ns"] = {"all_cores": rnd(cb.get("value")), "one_core_iterate": cb["one_core"]["iterate"]}
+    return s
 
 
 def run_probe(args):
@@ -543,53 +684,80 @@ def run_probe(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_sample(w, seconds_hint=False, it_sweeps=2000, prod_sweeps=500):
-    """The oracle as it stands on the host cores, on a bounded sample of the workload:
-    all p chains, one weight iteration of `it_sweeps` sweeps, the update, a production
-    run of `prod_sweeps` sweeps and the FP64 reweighting to every beta."""
+def cpu_phases(w, n_chains, it_sweeps, prod_sweeps, threads):
+    """The oracle as it stands on `threads` host cores: one weight iteration of
+    `it_sweeps` sweeps of `n_chains` chains, the update, `prod_sweeps` production sweeps,
+    and the FP64 reweighting to every beta; seconds of each phase."""
     from oracle import MucaOracle, reweight, sampler
+    sampler.set_threads(threads)
     betas = workloads.beta_grid(w["betas"])
-    o = MucaOracle(w["model"], w["L"], w["q"], w["p"], w["seed"])
+    o = MucaOracle(w["model"], w["L"], w["q"], n_chains, w["seed"])
     t0 = time.perf_counter()
     o.iterate(it_sweeps)
+    t1 = time.perf_counter()
     o.update_weights()
+    t2 = time.perf_counter()
     E, M = o.produce(prod_sweeps)
-    reweight.reweight_binned(w["model"], w["L"], w["q"], o.lnw,
-                             *reweight.bin_series(w["model"], w["L"], E, M), betas)
-    dt = time.perf_counter() - t0
-    att = w["p"] * w["L"] * w["L"] * (it_sweeps + prod_sweeps)
-    return {"value": att / (dt * 1e9), "unit": "attempts/ns", "cores": sampler.max_threads(),
-            "kind": "oracle", "seconds": dt,
-            "sample": "%s: all %d chains, 1 iteration x %d sweeps + update + %d production "
-                      "sweeps + FP64 reweight to %d betas" % (WORKLOAD, w["p"], it_sweeps,
-                                                             prod_sweeps, len(betas))}
+    t3 = time.perf_counter()
+    reweight.reweight_binned(w["model"], w["L"], w["q"], o.lnw, *reweight.bin_series(w["model"], w["L"], E, M),
+                             betas)
+    t4 = time.perf_counter()
+    return {"iterate": t1 - t0, "update": t2 - t1, "produce": t3 - t2, "reweight": t4 - t3,
+            "n_beta": len(betas)}
+
+
+def cpu_baseline(w):
+    """The oracle on the host cores, bounded: all 1024 chains on every core, 64 chains on
+    one core; attempts/ns of the iteration and production phases separately and FP64
+    reweighting betas/s; `value` is the whole all-core sample."""
+    from oracle import sampler
+    cores = sampler.max_threads()
+    V = w["L"] * w["L"]
+    it_s, pr_s = 400, 400
+    allc = cpu_phases(w, w["p"], it_s, pr_s, cores)
+    one = cpu_phases(w, 64, 100, 100, 1)
+    sampler.set_threads(cores)
+    att_all = w["p"] * V * (it_s + pr_s)
+    secs = allc["iterate"] + allc["update"] + allc["produce"] + allc["reweight"]
+    return {"value": att_all / (secs * 1e9), "unit": "attempts/ns", "cores": cores, "kind": "oracle",
+            "seconds": rnd(secs + one["iterate"] + one["update"] + one["produce"] + one["reweight"]),
+            "all_cores": {"iterate": rnd(w["p"] * V * it_s / allc["iterate"] / 1e9),
+                          "produce": rnd(w["p"] * V * pr_s / allc["produce"] / 1e9),
+                          "reweight_fp64_betas_per_s": rnd(allc["n_beta"] / allc["reweight"])},
+            "one_core": {"iterate": rnd(64 * V * 100 / one["iterate"] / 1e9),
+                         "produce": rnd(64 * V * 100 / one["produce"] / 1e9),
+                         "reweight_fp64_betas_per_s": rnd(one["n_beta"] / one["reweight"])},
+            "sample": "%s: all %d chains x (1 iteration of %d sweeps + update + %d production sweeps) + FP64 "
+                      "reweighting to %d betas on %d cores; 64 chains x (100 + 100 sweeps) on 1 core"
+                      % (WORKLOAD, w["p"], it_s, pr_s, allc["n_beta"], cores)}
 
 
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
+    from oracle import sampler
     w = workloads.WORKLOADS[WORKLOAD]
-    vals = []
+    cores = sampler.max_threads()
+    V = w["L"] * w["L"]
+    it_s, pr_s = 100, 20
+    secs = []
     for i in range(args.warmup + args.steps):
-        s = cpu_sample(w, it_sweeps=100, prod_sweeps=20)
+        ph = cpu_phases(w, w["p"], it_s, pr_s, cores)
         if i >= args.warmup:
-            vals.append(s)
-    secs = sum(v["seconds"] for v in vals)
-    att = w["p"] * w["L"] * w["L"] * 120 * len(vals)
-    value = att / (secs * 1e9)
-    base = dict(vals[-1])
-    base["value"] = value
+            secs.append(ph["iterate"] + ph["update"] + ph["produce"] + ph["reweight"])
+    att = w["p"] * V * (it_s + pr_s) * len(secs)
+    value = att / (sum(secs) * 1e9)
+    sample = ("%s: all %d chains, 1 iteration x %d sweeps + update + %d production sweeps + FP64 reweight "
+              "to %d betas per step" % (WORKLOAD, w["p"], it_s, pr_s, len(workloads.beta_grid(w["betas"]))))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/ns",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": secs * 1e3 / len(vals), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": sum(secs) * 1e3 / len(secs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64/int", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": w["L"], "p": w["p"],
-                   "sample_per_step": base["sample"]},
-        "cpu_baseline": base,
-        "e2e": {"value": value, "unit": "attempts/ns", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "config": {"workload": WORKLOAD, "L": w["L"], "p": w["p"], "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "attempts/ns", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "attempts/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 

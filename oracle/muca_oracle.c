@@ -355,6 +355,17 @@ int orc_muma_sweeps(int L, uint64_t seed, int phase, uint32_t iteration, uint32_
     return status ? -1 : 0;
 }
 
+/* Threads of the OpenMP loops over chains (the CPU-baseline timing runs 1 and all). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -43,6 +43,8 @@ def lib():
         L.orc_muma_sweeps.restype = ctypes.c_int
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = None
         _lib = L
     return _lib
 
@@ -117,6 +119,11 @@ def run_sweeps(model, L, q, seed, phase, iteration, sweep0, n_sweeps, chain0,
 
 def max_threads():
     return int(lib().orc_max_threads())
+
+
+def set_threads(n):
+    """Threads of the loops over chains from now on."""
+    lib().orc_set_threads(int(n))
 
 
 def run_muma_sweeps(L, seed, phase, iteration, sweep0, n_sweeps, chain0, spins, E, M, thr,
