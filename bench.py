@@ -53,15 +53,15 @@ SWEEP_SOURCES = ["paper_1212_3975_gb300/csrc/ws_bodies.cuh", "paper_1212_3975_gb
                  "paper_1212_3975_gb300/csrc/sweep_kernels.cu"]
 COUNTERS = {
     # Ising 64x64, one block per SM (p = 1024): profiles/ising_ws_sweep_L64_p1024.md
-    "ising_L64": {"source": "211dbf7fb5743202", "inst_per_attempt": 1.869,
+    "ising_L64": {"source": "7239a44f398aea87", "inst_per_attempt": 1.869,
                   "shared_wavefronts_per_attempt": 0.354, "traffic_bytes_per_launch": 681472},
     # Ising 64x64, compact staging, two blocks per SM (p = 9728):
     # profiles/ising_ws_compact_L64_p9728.md
-    "ising_L64_compact": {"source": "211dbf7fb5743202", "inst_per_attempt": 1.956,
+    "ising_L64_compact": {"source": "7239a44f398aea87", "inst_per_attempt": 1.956,
                           "shared_wavefronts_per_attempt": 0.381, "traffic_bytes_per_launch": 5170},
     # 8-Potts 32x32 (p = 4096): profiles/potts_ws_sweep_L32_p4096.md
-    "potts_L32": {"source": "earlier", "inst_per_attempt": 3.44, "shared_wavefronts_per_attempt": 0.52,
-                  "traffic_bytes_per_launch": 4320000},
+    "potts_L32": {"source": "7239a44f398aea87", "inst_per_attempt": 3.441, "shared_wavefronts_per_attempt": 0.521,
+                  "traffic_bytes_per_launch": 4321792},
 }
 # cycles per site of the Ising stream decider's loop run alone on one warp
 # (tests/gpu_decider_loop.cu, profiles/ising_decider_loop_replica.md)

@@ -130,10 +130,13 @@ int alloc_buffers(muca_ctx *c)
     if ((rc = dalloc(&c->d_H, nb, "histogram"))) return rc;
     if ((rc = dalloc(&c->d_samples, 3 * nb, "production sums"))) return rc;
     if ((rc = dalloc(&c->d_stats, 1, "stats"))) return rc;
-    // per-bin FP64 arrays (5), a float copy of ln Omega and the sampled range, each part
-    // 256-byte aligned
-    c->rw_bytes = ((5 * nb * sizeof(double) + 255) & ~(size_t)255) + nb * sizeof(float) + 2 * sizeof(int);
+    // per-bin part of the reweighting scratch (its setup counter must start at zero)
+    c->rw_bytes = rw_bin_part_bytes(nb);
     if ((rc = dalloc(reinterpret_cast<uint8_t **>(&c->d_rw), c->rw_bytes, "reweight scratch"))) return rc;
+    if (cudaMemset(c->d_rw, 0, c->rw_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MUCA_ERR_CUDA, "reweight scratch initialisation");
+    }
     if (cudaMallocHost(reinterpret_cast<void **>(&c->h_stats), sizeof(muca_iter_stats)) != cudaSuccess) {
         cudaGetLastError();
         return fail(MUCA_ERR_OOM, "pinned allocation failed");
@@ -461,10 +464,17 @@ int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
                                       cudaMemcpyHostToDevice, ctx->stream));
         d_betas = d_tmp + 4 * (size_t)n_beta;
     }
-    if ((rc = launch_reweight(ctx, d_betas, n_beta, precision, d_tmp))) return rc;
+    // device outputs are written in place; host (or null) outputs go through the scratch
     double *outs[4] = {e, C, absm, chi};
+    double *dev[4];
+    bool staged[4];
+    for (int k = 0; k < 4; ++k) {
+        staged[k] = !(outs[k] && is_device_ptr(outs[k]));
+        dev[k] = staged[k] ? d_tmp + (size_t)k * n_beta : outs[k];
+    }
+    if ((rc = launch_reweight(ctx, d_betas, n_beta, precision, dev))) return rc;
     for (int k = 0; k < 4; ++k)
-        if ((rc = copy_out(ctx, outs[k], d_tmp + (size_t)k * n_beta, sizeof(double) * n_beta))) return rc;
+        if (staged[k] && (rc = copy_out(ctx, outs[k], dev[k], sizeof(double) * n_beta))) return rc;
     return MUCA_OK;
 }
 

@@ -193,7 +193,7 @@ int launch_thresholds(muca_ctx *ctx);
 int launch_update(muca_ctx *ctx);
 int launch_stats(muca_ctx *ctx);
 int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision,
-                    double *d_out /* [4][n_beta] */);
+                    double *const out[4] /* e, C, absm, chi: device [n_beta] each */);
 SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs = true, bool allow_compact = true);
 int plan_flags(const SweepPlan &pl);  // MUCA_PLAN_* bit mask
 cudaError_t launch_batch_update(const BatchJob *d_jobs, int n_jobs, int max_thr, cudaStream_t st);
@@ -204,13 +204,26 @@ int launch_ktab(muca_ctx *ctx);
 // pieces.
 constexpr int kRwTile = 8;          // betas per tile
 constexpr int kRwMaxChunks = 32;    // bin chunks per tile at most
-constexpr size_t kRwTileParamsBytes = 48;
+constexpr size_t kRwTileParamsBytes = 72;
 constexpr size_t rw_align256(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t rw_bin_part_bytes(size_t nb) { return rw_align256(5 * nb * 8) + rw_align256(nb * 4 + 8); }
+// per-bin part: five FP64 arrays, five float arrays (ln Omega and mean |M| as float
+// pairs, the within-bin variance), the sampled range of every block of the preparation
+// kernel (256 bins each), and the completion counter of the setup kernel (zero between
+// calls: zeroed with the scratch, reset by its last user)
+constexpr size_t rw_bin_part_bytes(size_t nb)
+{
+    return rw_align256(5 * nb * 8) + 5 * rw_align256(nb * 4) + rw_align256(8 * ((nb + 255) / 256)) + 256;
+}
+// per-call part: tile parameters, shifts (FP64, and the float constants of every beta),
+// item offsets, the tiles' completion counters (each zeroed by its setup block), the
+// tile of every item, partial sums
 constexpr size_t rw_tile_part_bytes(size_t n_beta)
 {
     return rw_align256(kRwTileParamsBytes * ((n_beta + kRwTile - 1) / kRwTile)) + rw_align256(8 * n_beta) +
+           rw_align256(16 * n_beta) +
            rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile + 1)) +
+           rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile + 1)) +
+           rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile) * kRwMaxChunks) +
            8 * ((n_beta + kRwTile - 1) / kRwTile) * kRwMaxChunks * kRwTile * 6;
 }
 // allocation-free reweighting (reweight_noalloc.cu): the bins and betas per pass it

@@ -32,8 +32,8 @@
 // error, error-free additions) and w = exp2(a_hi) (1 + a_lo ln 2): at a beta far from
 // the sampled range the observables come from bins of relative weight ~1e-12, i.e.
 // |a| ~ 40 (log2 units), where a single float exponent would carry a relative error of
-// ~|a| 2^-24 into those weights.  Weights and column sums are FP32 within a thread and
-// a warp, FP64 across warps and chunks.
+// ~|a| 2^-24 into those weights.  Column sums are float pairs (an error-free addition
+// per term) within a thread and a warp, FP64 across warps and chunks.
 //
 // MUCA_BF16 (muca_reweight only): one block of 8 warps per tile of 16 betas (the M
 // dimension of mma.m16n8k16), an FP64 prologue per tile (reference bin, window,
@@ -43,7 +43,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <type_traits>
 
 #include "muca_internal.cuh"
 
@@ -323,16 +322,26 @@ constexpr double kLn2 = 0.6931471805599453;
 struct TileParams {
     int kT, lo, ch, nch;           // reference bin, first bin of the window, chunk size, chunks
     double lnOT, ET, x1T, betaT;
+    float lTh, lTl, x1Th, x1Tl;    // lnOmega and mean |M| of the reference bin as float pairs
+    float bTh, bTl;                // beta_T as a float pair
 };
 static_assert(sizeof(TileParams) == kRwTileParamsBytes, "tile parameter layout");
 
 struct RwScratch {
     BinData d;
-    float *lnOf;                   // float copy of lnOmega (-inf where unsampled)
-    int *range;                    // [2]: lowest and highest sampled bin
+    float *lnOf;                   // float copy of lnOmega (-inf where unsampled): high part
+    float *lnOl;                   //   and low part of lnOmega as a float pair
+    float *x1h, *x1l;              // mean |M| as a float pair
+    float *vf;                     // within-bin variance of |M| (float)
+    int2 *blkrange;                // [ceil(n_bins / 256)] lowest / highest sampled bin of each prep block
+    int nblk;
     TileParams *tiles;             // [n_tiles]
     double *c;                     // [n_beta] per-beta shift (ln units)
+    float4 *bc;                    // [n_beta] float constants: (beta - beta_T) log2 e as a pair, c log2 e
     int *off;                      // [n_tiles + 1] item offsets of the tiles
+    unsigned *cnt0;                // completion counter of the setup kernel (zero between calls)
+    unsigned *cnt;                 // [n_tiles] completion counters of the tiles (zeroed by the setup)
+    int *item_tile;                // [n_tiles * kRwMaxChunks] tile of every item
     double *part;                  // [n_tiles * kRwMaxChunks][kRwTile][6] partial sums
 };
 
@@ -341,30 +350,51 @@ __device__ __forceinline__ double bin_energy(int model, int V, int b)
     return model == MUCA_ISING ? (double)(4 * b - 2 * V) : (double)(b - 2 * V);
 }
 
-__global__ void rw_prep_kernel(const uint64_t *samples, const double *lnw, RwScratch r, int model, int V,
-                               int n_bins)
+// Per bin: FP64 lnOmega and means, the float copy, and the block's sampled range.
+__global__ void __launch_bounds__(256) rw_prep_kernel(const uint64_t *samples, const double *lnw, RwScratch r,
+                                                      int model, int V, int n_bins)
 {
+    __shared__ int s_lo[8], s_hi[8];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_bins) return;
-    const uint64_t n = samples[b];
-    r.d.E[b] = bin_energy(model, V, b);
-    if (n == 0) {
-        r.d.lnO[b] = -INFINITY;
-        r.lnOf[b] = -INFINITY;
-        r.d.x1[b] = r.d.x2[b] = r.d.v[b] = 0.0;
-        return;
+    int lo = 0x7FFFFFFF, hi = -1;
+    if (b < n_bins) {
+        const uint64_t n = samples[b];
+        r.d.E[b] = bin_energy(model, V, b);
+        if (n == 0) {
+            r.d.lnO[b] = -INFINITY;
+            r.lnOf[b] = -INFINITY;
+            r.lnOl[b] = r.x1h[b] = r.x1l[b] = r.vf[b] = 0.f;
+            r.d.x1[b] = r.d.x2[b] = r.d.v[b] = 0.0;
+        } else {
+            const double nd = (double)n;
+            const double l = __dsub_rn(log(nd), lnw[b]);
+            r.d.lnO[b] = l;
+            const float lh = (float)l;
+            r.lnOf[b] = lh;
+            r.lnOl[b] = (float)(l - (double)lh);
+            const double x1 = __ddiv_rn((double)samples[n_bins + b], nd);
+            const double x2 = __ddiv_rn((double)samples[2 * n_bins + b], nd);
+            r.d.x1[b] = x1;
+            r.d.x2[b] = x2;
+            r.d.v[b] = x2 - x1 * x1;
+            const float xh = (float)x1;
+            r.x1h[b] = xh;
+            r.x1l[b] = (float)(x1 - (double)xh);
+            r.vf[b] = (float)(x2 - x1 * x1);
+            lo = hi = b;
+        }
     }
-    const double nd = (double)n;
-    const double l = __dsub_rn(log(nd), lnw[b]);
-    r.d.lnO[b] = l;
-    r.lnOf[b] = (float)l;
-    const double x1 = __ddiv_rn((double)samples[n_bins + b], nd);
-    const double x2 = __ddiv_rn((double)samples[2 * n_bins + b], nd);
-    r.d.x1[b] = x1;
-    r.d.x2[b] = x2;
-    r.d.v[b] = x2 - x1 * x1;
-    atomicMin(&r.range[0], b);
-    atomicMax(&r.range[1], b);
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) { lo = min(lo, s_lo[w]); hi = max(hi, s_hi[w]); }
+        r.blkrange[blockIdx.x] = make_int2(lo, hi);
+    }
 }
 
 __device__ __forceinline__ void warp_argmax(float &v, int &i)
@@ -376,24 +406,88 @@ __device__ __forceinline__ void warp_argmax(float &v, int &i)
     }
 }
 
-// One block (256 threads) per tile: reference bin, window, chunks and per-beta shifts.
-__global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double *betas, int n_beta, int model, int V)
+// Exclusive prefix of the tiles' chunk counts, by one block of 256 threads (the last
+// setup block); tiles without a sampled bin get NaN observables here.
+__device__ void scan_tiles(RwScratch &r, int n_tiles, int n_beta, Observables o)
 {
-    __shared__ float s_v[8];
+    __shared__ int s_part[8];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < n_tiles; base += blockDim.x) {
+        const int T = base + (int)threadIdx.x;
+        const int v = T < n_tiles ? __ldcg(&r.tiles[T].nch) : 0;
+        if (T < n_tiles && v == 0)
+            for (int j = T * kRwTile; j < min(n_beta, (T + 1) * kRwTile); ++j)
+                o.e[j] = o.C[j] = o.absm[j] = o.chi[j] = NAN;
+        int x = v;
+        for (int k = 1; k < 32; k <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, k);
+            if (lane >= k) x += y;
+        }
+        if (lane == 31) s_part[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < 8 ? s_part[lane] : 0;
+            for (int k = 1; k < 8; k <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, k);
+                if (lane >= k) w += y;
+            }
+            if (lane < 8) s_part[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? s_part[warp - 1] : 0) + s_carry;
+        if (T < n_tiles) {
+            r.off[T] = incl - v;
+            for (int i = incl - v; i < incl; ++i) r.item_tile[i] = T;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) r.off[n_tiles] = s_carry;
+}
+
+// One block (256 threads) per tile: reference bin, window, chunks and per-beta shifts,
+// in two passes over the sampled bins; the block that finishes last numbers the chunks
+// of all tiles.
+__global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double *betas, int n_beta, int model, int V,
+                                                       Observables o)
+{
+    __shared__ float s_v[8], s_m[8][kRwTile];
     __shared__ int s_i[8], s_lo[8], s_hi[8];
+    __shared__ int s_last;
     const int T = blockIdx.x, j0 = T * kRwTile, nt = min(kRwTile, n_beta - j0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lo_s = r.range[0], hi_s = r.range[1];
+    if (threadIdx.x == 0) r.cnt[T] = 0u;  // the sums kernel counts this tile's chunks from zero
+    // sampled range of the bins, from the preparation blocks' ranges
+    int lo_s = 0x7FFFFFFF, hi_s = -1;
+    for (int i = threadIdx.x; i < r.nblk; i += blockDim.x) {
+        const int2 br = r.blkrange[i];
+        lo_s = min(lo_s, br.x);
+        hi_s = max(hi_s, br.y);
+    }
+    for (int k = 16; k > 0; k >>= 1) {
+        lo_s = min(lo_s, __shfl_xor_sync(0xffffffffu, lo_s, k));
+        hi_s = max(hi_s, __shfl_xor_sync(0xffffffffu, hi_s, k));
+    }
+    if (lane == 0) { s_lo[warp] = lo_s; s_hi[warp] = hi_s; }
+    __syncthreads();
+    lo_s = s_lo[0];
+    hi_s = s_hi[0];
+    for (int w = 1; w < 8; ++w) { lo_s = min(lo_s, s_lo[w]); hi_s = max(hi_s, s_hi[w]); }
+    __syncthreads();
     const double betaT = betas[j0 + nt / 2];
     const float bTf = (float)betaT;
-    // approximate reference bin (FP32 scan of the sampled range)
+    // pass 1: approximate reference bin (FP32)
     float best = -INFINITY;
     int kT = max(0, hi_s);  // replaced by a sampled bin whenever there is one
-    for (int b = lo_s + (int)threadIdx.x; b <= hi_s; b += blockDim.x) {
+#pragma unroll 4
+    for (int b = lo_s + (int)threadIdx.x; b <= hi_s; b += 256) {
         const float l = r.lnOf[b];
-        if (l == -INFINITY) continue;
         const float a = l - bTf * (float)bin_energy(model, V, b);
-        if (a > best) { best = a; kT = b; }
+        if (l != -INFINITY && a > best) { best = a; kT = b; }
     }
     warp_argmax(best, kT);
     if (lane == 0) { s_v[warp] = best; s_i[warp] = kT; }
@@ -402,29 +496,49 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
         best = lane < 8 ? s_v[lane] : -INFINITY;
         kT = lane < 8 ? s_i[lane] : max(0, hi_s);
         warp_argmax(best, kT);
-        if (lane == 0) { s_v[0] = best; s_i[0] = kT; }
+        if (lane == 0) s_i[0] = kT;
     }
     __syncthreads();
     kT = s_i[0];
     const float lTf = r.lnOf[kT];
     const double ETd = bin_energy(model, V, kT);
     const float ETf = (float)ETd;
-    float dbmax = 0.f;
-    for (int t = 0; t < nt; ++t) dbmax = fmaxf(dbmax, fabsf((float)(betas[j0 + t] - betaT)));
-    // window: bins that can reach e^-100 of the largest weight for some beta of the tile
-    // (approximate exponents, 2 units of margin)
+    float db[kRwTile], dbmax = 0.f;
+#pragma unroll
+    for (int t = 0; t < kRwTile; ++t) {
+        db[t] = t < nt ? (float)(betas[j0 + t] - betaT) : 0.f;
+        dbmax = fmaxf(dbmax, fabsf(db[t]));
+    }
+    // pass 2: the window (bins that can reach e^-100 of the largest weight for some beta
+    // of the tile, approximate exponents with 2 units of margin) and every beta's
+    // maximum exponent (attained inside the window)
     int lo = hi_s + 1, hi = lo_s - 1;
-    for (int b = lo_s + (int)threadIdx.x; b <= hi_s; b += blockDim.x) {
+    float mx[kRwTile];
+#pragma unroll
+    for (int t = 0; t < kRwTile; ++t) mx[t] = -INFINITY;
+#pragma unroll 2
+    for (int b = lo_s + (int)threadIdx.x; b <= hi_s; b += 256) {
         const float l = r.lnOf[b];
         if (l == -INFINITY) continue;
         const float dE = (float)bin_energy(model, V, b) - ETf;
-        if ((l - lTf) - bTf * dE + dbmax * fabsf(dE) >= (float)kCut - 2.f) { lo = min(lo, b); hi = max(hi, b); }
+        const float G = (l - lTf) - bTf * dE;
+        if (G + dbmax * fabsf(dE) >= (float)kCut - 2.f) { lo = min(lo, b); hi = max(hi, b); }
+#pragma unroll
+        for (int t = 0; t < kRwTile; ++t) mx[t] = fmaxf(mx[t], G - db[t] * dE);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    for (int k = 16; k > 0; k >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, k));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, k));
+#pragma unroll
+        for (int t = 0; t < kRwTile; ++t) mx[t] = fmaxf(mx[t], __shfl_xor_sync(0xffffffffu, mx[t], k));
     }
-    if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; }
+    __syncthreads();
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+#pragma unroll
+        for (int t = 0; t < kRwTile; ++t) s_m[warp][t] = mx[t];
+    }
     __syncthreads();
     lo = s_lo[0];
     hi = s_hi[0];
@@ -433,18 +547,14 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
         lo = 0;
         hi = -1;
     }
-    // per-beta shift: minus the approximate maximum of the exponent over the window
-    for (int t = warp; t < nt; t += 8) {
-        const float db = (float)(betas[j0 + t] - betaT);
-        float m = -INFINITY;
-        for (int b = lo + lane; b <= hi; b += 32) {
-            const float l = r.lnOf[b];
-            if (l == -INFINITY) continue;
-            const float dE = (float)bin_energy(model, V, b) - ETf;
-            m = fmaxf(m, (l - lTf) - bTf * dE - db * dE);
-        }
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) r.c[j0 + t] = -(double)m;
+    if ((int)threadIdx.x < nt) {
+        float m = s_m[0][threadIdx.x];
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, s_m[w][threadIdx.x]);
+        const double c = -(double)m;         // per-beta shift (ln units)
+        r.c[j0 + threadIdx.x] = c;
+        const double db2 = (betas[j0 + threadIdx.x] - betaT) * kLog2e;
+        const float dbh = (float)db2;
+        r.bc[j0 + threadIdx.x] = make_float4(dbh, (float)(db2 - (double)dbh), (float)(c * kLog2e), 0.f);
     }
     if (threadIdx.x == 0) {
         const int width = max(0, hi - lo + 1);
@@ -459,44 +569,25 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
         tp.ET = ETd;
         tp.x1T = r.d.x1[kT];
         tp.betaT = betaT;
+        tp.lTh = r.lnOf[kT];
+        tp.lTl = r.lnOl[kT];
+        tp.x1Th = r.x1h[kT];
+        tp.x1Tl = r.x1l[kT];
+        tp.bTh = (float)betaT;
+        tp.bTl = (float)(betaT - (double)tp.bTh);
         r.tiles[T] = tp;
     }
-}
-
-// Exclusive prefix of the tiles' chunk counts (one block).
-__global__ void __launch_bounds__(1024) rw_scan_kernel(RwScratch r, int n_tiles)
-{
-    __shared__ int s_part[32];
-    __shared__ int s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
+    // the last block to finish numbers the chunks (the classic last-block pattern: no
+    // block waits for another)
+    __threadfence();
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < n_tiles; base += blockDim.x) {
-        const int T = base + (int)threadIdx.x;
-        const int v = T < n_tiles ? r.tiles[T].nch : 0;
-        int x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_part[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int w = s_part[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_part[lane] = w;
-        }
-        __syncthreads();
-        const int incl = x + (warp > 0 ? s_part[warp - 1] : 0) + s_carry;
-        if (T < n_tiles) r.off[T] = incl - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = incl;
-        __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(r.cnt0, 1u) == (unsigned)gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        scan_tiles(r, gridDim.x, n_beta, o);
+        if (threadIdx.x == 0) *r.cnt0 = 0u;
     }
-    if (threadIdx.x == 0) r.off[n_tiles] = s_carry;
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -506,186 +597,248 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Persistent grid over the (tile, chunk) items.  FP64: exponents and weights in FP64;
-// FP32: compensated exponents, weights and sums in FP32 per thread, FP64 across warps.
+// Persistent grid over the (tile, chunk) items.  FP64: exponents, weights and sums in
+// FP64.  FP32: compensated exponents and weights in FP32; every column sum is kept as a
+// float pair (high part and the accumulated rounding errors of its additions), through
+// the thread's bins and the warp's tree, and combined in FP64 across warps.  (Plain
+// FP32 sums of 32 terms lost up to ~1e-6 relative on C and chi.)
 template <bool FP64>
-__global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double *betas, int n_beta, int n_tiles)
+__global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double *betas, int n_beta, int n_tiles,
+                                                      int model, int V, double mnorm, Observables o)
 {
-    using acc_t = typename std::conditional<FP64, double, float>::type;
     __shared__ double s_red[8][kRwTile][6];
-    __shared__ int s_T;
+    __shared__ float2 s_rf[8][kRwTile][6];
+    __shared__ int s_done;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int total = r.off[n_tiles];
+    const int dstep = model == MUCA_ISING ? 4 : 1;  // energy step between neighbouring bins
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        __syncthreads();  // s_red and s_T of the previous item are consumed
-        if (threadIdx.x == 0) {
-            int a = 0, b = n_tiles - 1;  // last tile with off <= item
-            while (a < b) {
-                const int m = (a + b + 1) >> 1;
-                if (r.off[m] <= item) a = m; else b = m - 1;
-            }
-            s_T = a;
-        }
-        __syncthreads();
-        const int T = s_T;
+        const int T = r.item_tile[item];
         const TileParams tp = r.tiles[T];
         const int chunk = item - r.off[T];
         const int j0 = T * kRwTile, nt = min(kRwTile, n_beta - j0);
         const int b0 = tp.lo + chunk * tp.ch;
         const int b1 = min(b0 + tp.ch, tp.lo + tp.nch * tp.ch);
-        // per-beta constants of the tile
-        double cd[kRwTile], dbd[kRwTile];
-        float ch_[kRwTile], dbh[kRwTile], dbl[kRwTile];
+        if (FP64) {
+            double cd[kRwTile], dbd[kRwTile];
 #pragma unroll
-        for (int t = 0; t < kRwTile; ++t) {
-            const bool ok = t < nt;
-            cd[t] = ok ? r.c[j0 + t] : -1e300;
-            dbd[t] = ok ? betas[j0 + t] - tp.betaT : 0.0;
-            const double dbl2 = dbd[t] * kLog2e;
-            dbh[t] = (float)dbl2;
-            dbl[t] = (float)(dbl2 - (double)dbh[t]);
-            ch_[t] = ok ? (float)(cd[t] * kLog2e) : -1e30f;
-        }
-        acc_t acc[kRwTile][6];
+            for (int t = 0; t < kRwTile; ++t) {
+                const bool ok = t < nt;
+                cd[t] = ok ? r.c[j0 + t] : -1e300;
+                dbd[t] = ok ? betas[j0 + t] - tp.betaT : 0.0;
+            }
+            double acc[kRwTile][6];
 #pragma unroll
-        for (int t = 0; t < kRwTile; ++t)
+            for (int t = 0; t < kRwTile; ++t)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[t][k] = 0;
-        for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
-            const double l = r.d.lnO[b];
-            if (l == -INFINITY) continue;
-            const double dEd = r.d.E[b] - tp.ET;
-            const double G = __dsub_rn(__dsub_rn(l, tp.lnOT), __dmul_rn(tp.betaT, dEd));
-            const double dx = r.d.x1[b] - tp.x1T, vb = r.d.v[b];
-            if (FP64) {
+                for (int k = 0; k < 6; ++k) acc[t][k] = 0.0;
+            for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
+                const double l = r.d.lnO[b];
+                if (l == -INFINITY) continue;
+                const double dEd = (double)(dstep * (b - tp.kT));
+                const double G = __dsub_rn(__dsub_rn(l, tp.lnOT), __dmul_rn(tp.betaT, dEd));
+                const double dx = r.d.x1[b] - tp.x1T;
+                const double cols[6] = {1.0, dEd, dEd * dEd, dx, dx * dx, r.d.v[b]};
 #pragma unroll
                 for (int t = 0; t < kRwTile; ++t) {
                     const double a = __fma_rn(-dbd[t], dEd, G + cd[t]);
                     if (a < kCut) continue;
                     const double w = exp(a);
-                    acc[t][0] += (acc_t)w;
-                    acc[t][1] += (acc_t)(w * dEd);
-                    acc[t][2] += (acc_t)(w * dEd * dEd);
-                    acc[t][3] += (acc_t)(w * dx);
-                    acc[t][4] += (acc_t)(w * dx * dx);
-                    acc[t][5] += (acc_t)(w * vb);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc[t][k] = __fma_rn(w, cols[k], acc[t][k]);
                 }
-            } else {
-                const double G2 = G * kLog2e;
-                const float Gh = (float)G2, Gl = (float)(G2 - (double)Gh);
-                const float dE = (float)dEd, dxf = (float)dx, vf = (float)vb;
-                const float dE2 = dE * dE, dx2 = dxf * dxf;
+            }
+#pragma unroll
+            for (int t = 0; t < kRwTile; ++t)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    double x = acc[t][k];
+                    for (int q = 16; q > 0; q >>= 1) x += __shfl_xor_sync(0xffffffffu, x, q);
+                    if (lane == 0) s_red[warp][t][k] = x;
+                }
+            __syncthreads();
+            if ((int)threadIdx.x < kRwTile * 6) {
+                const int t = threadIdx.x / 6, k = threadIdx.x % 6;
+                double x = 0.0;
+                for (int w = 0; w < 8; ++w) x += s_red[w][t][k];
+                r.part[((size_t)item * kRwTile + t) * 6 + k] = x;
+            }
+        } else {
+            // FP32 only: the tile's reference and every beta's constants come as floats
+            float dbh[kRwTile], dbl[kRwTile], chv[kRwTile];
+#pragma unroll
+            for (int t = 0; t < kRwTile; ++t) {
+                const float4 kc = t < nt ? r.bc[j0 + t] : make_float4(0.f, 0.f, -1e30f, 0.f);
+                dbh[t] = kc.x;
+                dbl[t] = kc.y;
+                chv[t] = kc.z;
+            }
+            const float L2h = (float)kLog2e, L2l = (float)(kLog2e - (double)(float)kLog2e);
+            float hi[kRwTile][6], lo[kRwTile][6];
+#pragma unroll
+            for (int t = 0; t < kRwTile; ++t)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) hi[t][k] = lo[t][k] = 0.f;
+            for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
+                const float lh = r.lnOf[b];
+                if (lh == -INFINITY) continue;
+                const float dE = (float)(dstep * (b - tp.kT));  // exact
+                // G = (lnOmega_b - lnOmega_kT) - beta_T dE as a float pair, in log2 units
+                float d1, e1, g1, e2;
+                two_sum(lh, -tp.lTh, d1, e1);
+                const float dlo = __fadd_rn(e1, __fsub_rn(r.lnOl[b], tp.lTl));
+                const float p = __fmul_rn(tp.bTh, dE);
+                const float pe = __fmaf_rn(tp.bTh, dE, -p);
+                const float q = __fmul_rn(tp.bTl, dE);
+                two_sum(d1, -p, g1, e2);
+                const float glo = __fsub_rn(__fsub_rn(__fadd_rn(e2, dlo), pe), q);
+                const float Gh = __fmul_rn(g1, L2h);
+                const float Gl = __fadd_rn(__fmaf_rn(g1, L2h, -Gh), __fadd_rn(__fmul_rn(g1, L2l), __fmul_rn(glo, L2h)));
+                // mean |M| relative to the reference bin
+                float xa, xe;
+                two_sum(r.x1h[b], -tp.x1Th, xa, xe);
+                const float dxf = __fadd_rn(xa, __fadd_rn(xe, __fsub_rn(r.x1l[b], tp.x1Tl)));
+                const float cols[6] = {1.f, dE, __fmul_rn(dE, dE), dxf, __fmul_rn(dxf, dxf), r.vf[b]};
 #pragma unroll
                 for (int t = 0; t < kRwTile; ++t) {
                     // a = (Gh + Gl) + c - (dbh + dbl) dE as a float pair
-                    const float p = __fmul_rn(dbh[t], dE);
-                    const float pe = __fmaf_rn(dbh[t], dE, -p);
-                    const float q = __fmul_rn(dbl[t], dE);
-                    float s1, e1, s2, e2;
-                    two_sum(Gh, ch_[t], s1, e1);
-                    two_sum(s1, -p, s2, e2);
-                    const float lo = __fsub_rn(__fadd_rn(__fadd_rn(e1, e2), Gl), __fadd_rn(pe, q));
-                    const float ah = __fadd_rn(s2, lo);
-                    const float al = __fsub_rn(lo, __fsub_rn(ah, s2));
+                    const float pt = __fmul_rn(dbh[t], dE);
+                    const float pte = __fmaf_rn(dbh[t], dE, -pt);
+                    const float qt = __fmul_rn(dbl[t], dE);
+                    float s1, f1, s2, f2;
+                    two_sum(Gh, chv[t], s1, f1);
+                    two_sum(s1, -pt, s2, f2);
+                    const float rl = __fsub_rn(__fadd_rn(__fadd_rn(f1, f2), Gl), __fadd_rn(pte, qt));
+                    const float ah = __fadd_rn(s2, rl);
+                    const float al = __fsub_rn(rl, __fsub_rn(ah, s2));
                     const float w0 = exp2f(ah);
                     const float w = __fmaf_rn(w0, al * (float)kLn2, w0);
-                    acc[t][0] += (acc_t)w;
-                    acc[t][1] = __fmaf_rn(w, dE, acc[t][1]);
-                    acc[t][2] = __fmaf_rn(w, dE2, acc[t][2]);
-                    acc[t][3] = __fmaf_rn(w, dxf, acc[t][3]);
-                    acc[t][4] = __fmaf_rn(w, dx2, acc[t][4]);
-                    acc[t][5] = __fmaf_rn(w, vf, acc[t][5]);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        float sum, err;
+                        two_sum(hi[t][k], __fmul_rn(w, cols[k]), sum, err);
+                        hi[t][k] = sum;
+                        lo[t][k] = __fadd_rn(lo[t][k], err);
+                    }
                 }
             }
-        }
-        // reduce: within the warp in the accumulation type, across warps in FP64
 #pragma unroll
-        for (int t = 0; t < kRwTile; ++t)
+            for (int t = 0; t < kRwTile; ++t)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                acc_t x = acc[t][k];
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0) s_red[warp][t][k] = (double)x;
+                for (int k = 0; k < 6; ++k) {
+                    float h = hi[t][k], e = lo[t][k];
+                    for (int q = 16; q > 0; q >>= 1) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, h, q);
+                        const float oe = __shfl_xor_sync(0xffffffffu, e, q);
+                        float sum, err;
+                        two_sum(h, oh, sum, err);
+                        h = sum;
+                        e = __fadd_rn(__fadd_rn(e, oe), err);
+                    }
+                    if (lane == 0) s_rf[warp][t][k] = make_float2(h, e);
+                }
+            __syncthreads();
+            if ((int)threadIdx.x < kRwTile * 6) {
+                const int t = threadIdx.x / 6, k = threadIdx.x % 6;
+                float h = s_rf[0][t][k].x, e = s_rf[0][t][k].y;
+                for (int w = 1; w < 8; ++w) {
+                    float sum, err;
+                    two_sum(h, s_rf[w][t][k].x, sum, err);
+                    h = sum;
+                    e = __fadd_rn(__fadd_rn(e, s_rf[w][t][k].y), err);
+                }
+                r.part[((size_t)item * kRwTile + t) * 6 + k] = (double)h + (double)e;
             }
+        }
+        // the block that completes a tile's last chunk combines the tile's partial sums
+        // in chunk order (deterministic) and writes its observables
+        __threadfence();
         __syncthreads();
-        if ((int)threadIdx.x < kRwTile * 6) {
-            const int t = threadIdx.x / 6, k = threadIdx.x % 6;
-            double x = 0.0;
-            for (int w = 0; w < 8; ++w) x += s_red[w][t][k];
-            r.part[((size_t)item * kRwTile + t) * 6 + k] = x;
+        if (threadIdx.x == 0) s_done = atomicAdd(&r.cnt[T], 1u) + 1u == (unsigned)tp.nch;
+        __syncthreads();
+        if (s_done) {
+            __threadfence();
+            if ((int)threadIdx.x < nt) {
+                const int t = threadIdx.x;
+                double S[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = r.off[T]; i < r.off[T] + tp.nch; ++i)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) S[k] += __ldcg(&r.part[((size_t)i * kRwTile + t) * 6 + k]);
+                write_obs(o, j0 + t, betas[j0 + t], tp.ET, tp.x1T, S[0], S[1], S[2], S[3], S[4], S[5], V, mnorm);
+            }
         }
     }
-}
-
-// Per beta: partial sums of its tile in chunk order, then the observables.
-__global__ void rw_combine_kernel(RwScratch r, const double *betas, int n_beta, int V, double mnorm, Observables o)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_beta) return;
-    const int T = j / kRwTile, t = j % kRwTile;
-    const TileParams tp = r.tiles[T];
-    double S[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = r.off[T]; i < r.off[T + 1]; ++i)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) S[k] += r.part[((size_t)i * kRwTile + t) * 6 + k];
-    write_obs(o, j, betas[j], tp.ET, tp.x1T, S[0], S[1], S[2], S[3], S[4], S[5], V, mnorm);
 }
 
 }  // namespace
 
 namespace {
 
-// setup, scan, sums and combine of one batch of betas (the per-bin arrays of `r` are
-// prepared); `n_sm` sizes the persistent grid of the sums
+// setup (with the chunk numbering) and sums (with the per-tile combine) of one batch of
+// betas, the per-bin arrays of `r` prepared; `n_sm` sizes the persistent grid of the sums
 cudaError_t launch_tiles(const RwScratch &r, const double *d_betas, int n_beta, int precision, int model, int V,
                          double mnorm, const Observables &o, int n_sm, cudaStream_t st)
 {
     const int n_tiles = (n_beta + kRwTile - 1) / kRwTile;
-    rw_setup_kernel<<<n_tiles, 256, 0, st>>>(r, d_betas, n_beta, model, V);
-    rw_scan_kernel<<<1, 1024, 0, st>>>(r, n_tiles);
+    rw_setup_kernel<<<n_tiles, 256, 0, st>>>(r, d_betas, n_beta, model, V, o);
     const int grid = std::max(1, std::min(n_tiles * kRwMaxChunks, 4 * n_sm));
     if (precision == MUCA_FP64)
-        rw_sums_kernel<true><<<grid, 256, 0, st>>>(r, d_betas, n_beta, n_tiles);
+        rw_sums_kernel<true><<<grid, 256, 0, st>>>(r, d_betas, n_beta, n_tiles, model, V, mnorm, o);
     else
-        rw_sums_kernel<false><<<grid, 256, 0, st>>>(r, d_betas, n_beta, n_tiles);
-    rw_combine_kernel<<<(n_beta + 127) / 128, 128, 0, st>>>(r, d_betas, n_beta, V, mnorm, o);
+        rw_sums_kernel<false><<<grid, 256, 0, st>>>(r, d_betas, n_beta, n_tiles, model, V, mnorm, o);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) note_launches(4);
+    if (e == cudaSuccess) note_launches(2);
     return e;
 }
 
 size_t align256(size_t bytes) { return rw_align256(bytes); }
-size_t tile_part_bytes(int n_beta) { return rw_tile_part_bytes((size_t)n_beta); }
 
-RwScratch carve(void *bins, size_t nb, void *tiles, int n_beta)
+// Pointers into the scratch.  The per-bin part is laid out for `cap` bins (>= nb), so
+// that the setup counter at its end stays at one place for every lattice served.
+RwScratch carve(void *bins, size_t cap, size_t nb, void *tiles, int n_beta)
 {
     RwScratch r;
     char *pb = reinterpret_cast<char *>(bins);
     double *base = reinterpret_cast<double *>(pb);
-    r.d = BinData{base, base + nb, base + 2 * nb, base + 3 * nb, base + 4 * nb};
-    r.lnOf = reinterpret_cast<float *>(pb + align256(5 * nb * sizeof(double)));
-    r.range = reinterpret_cast<int *>(r.lnOf + nb);
+    r.d = BinData{base, base + cap, base + 2 * cap, base + 3 * cap, base + 4 * cap};
+    pb += align256(5 * cap * sizeof(double));
+    r.lnOf = reinterpret_cast<float *>(pb);
+    pb += align256(cap * sizeof(float));
+    r.lnOl = reinterpret_cast<float *>(pb);
+    pb += align256(cap * sizeof(float));
+    r.x1h = reinterpret_cast<float *>(pb);
+    pb += align256(cap * sizeof(float));
+    r.x1l = reinterpret_cast<float *>(pb);
+    pb += align256(cap * sizeof(float));
+    r.vf = reinterpret_cast<float *>(pb);
+    pb += align256(cap * sizeof(float));
+    r.blkrange = reinterpret_cast<int2 *>(pb);
+    r.nblk = (int)((nb + 255) / 256);
+    pb += align256(sizeof(int2) * ((cap + 255) / 256));
+    r.cnt0 = reinterpret_cast<unsigned *>(pb);
     const size_t n_tiles = (size_t)(n_beta + kRwTile - 1) / kRwTile;
     char *pt = reinterpret_cast<char *>(tiles);
     r.tiles = reinterpret_cast<TileParams *>(pt);
     pt += align256(sizeof(TileParams) * n_tiles);
     r.c = reinterpret_cast<double *>(pt);
     pt += align256(sizeof(double) * n_beta);
+    r.bc = reinterpret_cast<float4 *>(pt);
+    pt += align256(sizeof(float4) * n_beta);
     r.off = reinterpret_cast<int *>(pt);
     pt += align256(sizeof(int) * (n_tiles + 1));
+    r.cnt = reinterpret_cast<unsigned *>(pt);
+    pt += align256(sizeof(unsigned) * (n_tiles + 1));  // (one spare entry)
+    r.item_tile = reinterpret_cast<int *>(pt);
+    pt += align256(sizeof(int) * n_tiles * kRwMaxChunks);
     r.part = reinterpret_cast<double *>(pt);
     return r;
 }
 
-// per-bin preparation, including the sampled range (reset first)
 cudaError_t launch_prep(const RwScratch &r, const uint64_t *samples, const double *lnw, int model, int V, int nb,
                         cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(r.range, 0x7F, sizeof(int), st);  // lowest bin starts at 0x7F7F7F7F
-    if (e == cudaSuccess) e = cudaMemsetAsync(r.range + 1, 0xFF, sizeof(int), st);  // highest at -1
-    if (e != cudaSuccess) return e;
-    rw_prep_kernel<<<(nb + 255) / 256, 256, 0, st>>>(samples, lnw, r, model, V, nb);
-    e = cudaGetLastError();
+    rw_prep_kernel<<<r.nblk, 256, 0, st>>>(samples, lnw, r, model, V, nb);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) note_launches(1);
     return e;
 }
@@ -704,8 +857,12 @@ cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, co
     const int V = L * L;
     const int nb = n_bins_of(model, L);
     char *base = reinterpret_cast<char *>(scratch);
-    RwScratch r = carve(base, nb, base + rw_bin_part_bytes(kNoallocMaxBins), kNoallocBetasPerPass);
-    cudaError_t e = launch_prep(r, samples, lnw, model, V, nb, st);
+    RwScratch r = carve(base, kNoallocMaxBins, nb, base + rw_bin_part_bytes(kNoallocMaxBins), kNoallocBetasPerPass);
+    // the setup counter is cleared by every call here: calls that overlapped on the GPU
+    // (a race the caller must avoid) then spoil their own results only
+    cudaError_t e = cudaMemsetAsync(r.cnt0, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    e = launch_prep(r, samples, lnw, model, V, nb, st);
     if (e != cudaSuccess) return e;
     const double mnorm = model == MUCA_ISING ? (double)V : (double)(q - 1) * V;
     for (int j0 = 0; j0 < n_beta; j0 += kNoallocBetasPerPass) {
@@ -718,12 +875,12 @@ cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, co
     return cudaSuccess;
 }
 
-int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision, double *d_out)
+int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precision, double *const out[4])
 {
     const size_t nb = ctx->n_bins;
     double *base = reinterpret_cast<double *>(ctx->d_rw);
     BinData d{base, base + nb, base + 2 * nb, base + 3 * nb, base + 4 * nb};
-    Observables o{d_out, d_out + n_beta, d_out + 2 * n_beta, d_out + 3 * n_beta};
+    Observables o{out[0], out[1], out[2], out[3]};
     const double mnorm = ctx->model == MUCA_ISING ? (double)ctx->V : (double)(ctx->q - 1) * ctx->V;
     if (precision == MUCA_BF16) {
         prep_kernel<<<(ctx->n_bins + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_samples, ctx->d_lnw_prod, d,
@@ -738,8 +895,8 @@ int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precis
     }
     if (precision != MUCA_FP64 && precision != MUCA_FP32)
         return fail(MUCA_ERR_ARG, "precision must be MUCA_FP64, MUCA_FP32 or MUCA_BF16");
-    // per-call scratch: tile parameters, shifts, item offsets, partial sums
-    const size_t need = tile_part_bytes(n_beta);
+    // per-call scratch: tile parameters, shifts, item offsets, counters, partial sums
+    const size_t need = rw_tile_part_bytes((size_t)n_beta);
     if (ctx->rwtile_bytes < need) {
         MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         if (ctx->d_rwtile) cudaFree(ctx->d_rwtile);
@@ -751,7 +908,7 @@ int launch_reweight(muca_ctx *ctx, const double *d_betas, int n_beta, int precis
         }
         ctx->rwtile_bytes = need;
     }
-    const RwScratch r = carve(ctx->d_rw, nb, ctx->d_rwtile, n_beta);
+    const RwScratch r = carve(ctx->d_rw, nb, nb, ctx->d_rwtile, n_beta);
     MUCA_CUDA_TRY(launch_prep(r, ctx->d_samples, ctx->d_lnw_prod, ctx->model, ctx->V, ctx->n_bins, ctx->stream));
     MUCA_CUDA_TRY(launch_tiles(r, d_betas, n_beta, precision, ctx->model, ctx->V, mnorm, o, ctx->n_sm, ctx->stream));
     return MUCA_OK;

@@ -10,7 +10,7 @@
 //
 // The array is part of this library's device image: once the image is loaded on a
 // GPU (with CUDA's default lazy loading, at the first call on that device, which
-// therefore needs kNoallocScratchBytes = 1,515,520 bytes of free device memory once;
+// therefore needs kNoallocScratchBytes = 1,798,144 bytes of free device memory once;
 // make that first call at start-up, before any stream capture), the GPU holds it until
 // the process exits.  Host code may not use the array's name as a device address;
 // every call looks the address up with cudaGetSymbolAddress for the current device, so
@@ -26,12 +26,13 @@ using muca::kNoallocMaxBins;
 
 // Scratch of the tiled reweighting kernels for at most kNoallocMaxBins bins and
 // kNoallocBetasPerPass betas per pass: per-bin arrays (ln n - ln W, E, mean |M|, mean
-// M^2, within-bin variance of |M|, a float copy of the first, the sampled range) and
-// per-pass tile parameters, shifts and partial sums.  Every entry a call reads is
-// written by the same call first (the sampled range is reset by each call), so
-// nothing has to start at zero.
+// M^2, within-bin variance of |M|, a float copy of the first, the sampled range of
+// each block of bins, the setup kernel's completion counter) and per-pass tile
+// parameters, shifts, completion counters and partial sums.  Every entry a call reads
+// is written or cleared by the same call first, so nothing has to start at zero.
 static __device__ __align__(256) double g_noalloc_scratch[muca::kNoallocScratchBytes / sizeof(double)];
 static_assert(muca::kNoallocScratchBytes % sizeof(double) == 0, "scratch size");
+static_assert(muca::kNoallocScratchBytes == 1798144, "the documented size of the scratch");
 
 // device (or managed) memory that the current device `dev` can use
 bool device_pointer_on(const void *p, int dev)

@@ -164,9 +164,11 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
 {
 #define LAT(k) lp[(size_t)(k) * ls]
     const int L = a.L, RW = a.row_words;
+    // (fields of `a` are read once here: in the batched kernel `a` lives in shared memory,
+    // and every named barrier would make the compiler read it again)
+    const char *const ktab_b = reinterpret_cast<const char *>(a.ktab) - tab_s;
     auto tload = [&](uint32_t o) -> uint32_t {
-        return TSMEM ? lds_u32(o)
-                     : ldg_nc_u32(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + o - tab_s));
+        return TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(ktab_b + o));
     };
     auto row_up = [&](int y) { return (y == 0 ? L - 1 : y - 1) * RW; };    // row above: updated
     auto row_down = [&](int y) { return (y == L - 1 ? 0 : y + 1) * RW; };  // row below: old (new for y = L-1)
@@ -374,9 +376,11 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         const int pr = warp - 1;
         uint32_t k1r[10];
         philox_round_keys((uint32_t)c, k1r);
+        const uint32_t key0 = a.key0, iter = a.iteration, ctr3 = a.ctr3, sweep0 = a.sweep0;
+        const int n_sweeps = a.n_sweeps;
         int it = 0;
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
+        for (int sw = 0; sw < n_sweeps; ++sw) {
+            const uint32_t ctr1 = sweep0 + (uint32_t)sw;
             int site = 0;
             for (int y = 0; y < L; ++y) {
                 for (int w = 0; w < RW; ++w, ++it) {
@@ -388,9 +392,8 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                     // dependency chains interleave
 #pragma unroll 4
                     for (int gi = pr; gi < (nb >> 2); gi += NP) {
-                        uint4 b = philox4x32_10_rk(make_uint4((uint32_t)(site >> 2) + (uint32_t)gi, ctr1, a.iteration,
-                                                              a.ctr3),
-                                                   a.key0, k1r);
+                        uint4 b = philox4x32_10_rk(make_uint4((uint32_t)(site >> 2) + (uint32_t)gi, ctr1, iter, ctr3),
+                                                   key0, k1r);
                         // clamped so that u < A decides (A = 2^32-1 always accepts);
                         // padding chains get 2^32-1, which never accepts
                         const uint32_t cap = active ? 0xFFFFFFFEu : 0xFFFFFFFFu;
@@ -412,9 +415,8 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
 #define LAT(k) lp[(size_t)(k) * ls]
         // table addresses: shared-memory addresses, or byte offsets into the global table
         const uint32_t tab_s = TSMEM ? (uint32_t)__cvta_generic_to_shared(s_tab) : 0u;
-#define TAB_BYTES(o)                 \
-    (TSMEM ? lds_u32(tab_s + (o))    \
-           : ldg_nc_u32(reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(a.ktab) + (o))))
+        const char *const ktab_g = reinterpret_cast<const char *>(a.ktab);
+#define TAB_BYTES(o) (TSMEM ? lds_u32(tab_s + (o)) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(ktab_g + (o))))
         const int bin0 = active ? (a.E[c] + 2 * V) >> 2 : (V >> 1);
         uint32_t bin20 = 20u * (uint32_t)bin0;  // 4*5*bin before the previous decision
         uint32_t d20p = 0u;                     // its change if the previous attempt was accepted
@@ -477,9 +479,9 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                         uint32_t K0, K1, D0, D1;
                         site_consts(0, K0, K1, D0, D1);
                         uint32_t A0 = TSMEM ? lds_u32(P0 + K0) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
-                                                                      reinterpret_cast<const char *>(a.ktab) + P0 + K0 - tab_s));
+                                                                      ktab_g + P0 + K0 - tab_s));
                         uint32_t A1 = TSMEM ? lds_u32(P1 + K1) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
-                                                                      reinterpret_cast<const char *>(a.ktab) + P1 + K1 - tab_s));
+                                                                      ktab_g + P1 + K1 - tab_s));
                         // draws of the word: group g+1 is loaded while group g is decided
                         uint4 blk = src[0], blk_next = src[32];
 #pragma unroll
@@ -499,9 +501,9 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                                 const uint32_t o0 = ap ? P1 + K0n : P0 + K0n;
                                 const uint32_t o1 = ap ? P1 + D1 + K1n : P0 + D0 + K1n;
                                 A0n = TSMEM ? lds_u32(o0) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
-                                                               reinterpret_cast<const char *>(a.ktab) + o0 - tab_s));
+                                                               ktab_g + o0 - tab_s));
                                 A1n = TSMEM ? lds_u32(o1) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(
-                                                               reinterpret_cast<const char *>(a.ktab) + o1 - tab_s));
+                                                               ktab_g + o1 - tab_s));
                             }
                             const uint32_t A = ap ? A1 : A0;
                             const bool acc = u < A;
@@ -824,7 +826,9 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     // A producer reads row y+1 (old) and, for the last row, row 0 of the current sweep
     // (new), so it may run at most L - 1 rows of slots ahead: 3 <= spr * (L - 1) for L >= 4.
     constexpr int RD = kPottsRing;
-#define LAT(k) (*(LSMEM ? &s_lat[(k) * 32 + lane] : &a.lat[(size_t)(k) * a.p_pad + c]))
+    uint32_t *const glat = a.lat + c;
+    const size_t gstride = (size_t)a.p_pad;
+#define LAT(k) (*(LSMEM ? &s_lat[(k) * 32 + lane] : &glat[(size_t)(k) * gstride]))
 
     if (vw >= 1 && vw <= kPottsRing) {
         // ---------------- producers ----------------------------------------------
@@ -832,12 +836,13 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
         uint32_t k1r[10];
         philox_round_keys((uint32_t)c, k1r);
         const uint32_t cap = active ? 0xFFFFFFFEu : 0xFFFFFFFFu;
+        const uint32_t key0 = a.key0, iter = a.iteration, ctr3 = a.ctr3, sweep0 = a.sweep0;
         auto draw = [&](uint32_t x) { return active ? min(x, cap) : cap; };
         // proposal offset floor(7 w / 2^32) in 0..6, exactly: 7w = 8w - w
         auto offset7 = [](uint32_t x) { return (x >> 29) - ((x << 3) < x ? 1u : 0u); };
         int it = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            const uint32_t ctr1 = a.sweep0 + (uint32_t)sw;
+            const uint32_t ctr1 = sweep0 + (uint32_t)sw;
             for (int y = 0; y < L; ++y) {
                 const int kr = y * RW, kd = (y == L - 1 ? 0 : y + 1) * RW;
                 for (int w0 = 0; w0 < RW; w0 += kPottsSlotWords, ++it) {
@@ -859,9 +864,8 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                             const uint32_t Rn = lastw ? 0xFFu : LAT(kr + w + 1);
                             const uint32_t D = LAT(kd + w);
                             const uint32_t g = (uint32_t)(y * L + 4 * w) >> 1;
-                            const uint4 b0 = philox4x32_10_rk(make_uint4(g, ctr1, a.iteration, a.ctr3), a.key0, k1r);
-                            const uint4 b1 =
-                                philox4x32_10_rk(make_uint4(g + 1u, ctr1, a.iteration, a.ctr3), a.key0, k1r);
+                            const uint4 b0 = philox4x32_10_rk(make_uint4(g, ctr1, iter, ctr3), key0, k1r);
+                            const uint4 b1 = philox4x32_10_rk(make_uint4(g + 1u, ctr1, iter, ctr3), key0, k1r);
                             const uint32_t off = offset7(b0.y) | (offset7(b0.w) << 8) | (offset7(b1.y) << 16) |
                                                  (offset7(b1.w) << 24);
                             const uint32_t SN = (R + 0x01010101u + off) & 0x07070707u;  // (s + 1 + off) mod 8
