@@ -43,6 +43,7 @@ __device__ __forceinline__ SweepArgs batch_args(const BatchJob &j, int n_sweeps,
     a.q = j.q;
     a.p = j.p;
     a.p_pad = j.p_pad;
+    a.cpg = 32;
     a.row_words = j.row_words;
     a.lat_words = j.lat_words;
     a.n_bins = j.n_bins;
@@ -441,6 +442,7 @@ extern "C" {
 
 int muca_batch_create(muca_batch **out, const muca_job *jobs, int n_jobs, const muca_config *cfg, void *cuda_stream)
 {
+    MUCA_RANGE("muca_batch_create");
     if (!out) return fail(MUCA_ERR_ARG, "out is null");
     *out = nullptr;
     if (!jobs || n_jobs < 1 || n_jobs > 4096) return fail(MUCA_ERR_ARG, "need 1..4096 jobs");
@@ -460,14 +462,20 @@ int muca_batch_create(muca_batch **out, const muca_job *jobs, int n_jobs, const 
     }
     b->staging = cfg ? cfg->staging : MUCA_STAGING_AUTO;
     b->ctx.assign(n_jobs, nullptr);
+    // the persistent kernel's work units are groups of 32 chains
+    muca_config jc{MUCA_RECURSION_ACCUMULATED, 0, 0, MUCA_STAGING_AUTO, MUCA_ENSEMBLE_ENERGY, 0.0};
+    if (cfg) jc = *cfg;
+    if (jc.chains_per_block == 0) jc.chains_per_block = 32;
+    b->cfg = jc;
     for (int i = 0; i < n_jobs; ++i) {
-        int rc = muca_init(&b->ctx[i], jobs[i].model, jobs[i].L, jobs[i].q, jobs[i].p, jobs[i].seed, cfg, b->stream);
+        int rc = muca_init(&b->ctx[i], jobs[i].model, jobs[i].L, jobs[i].q, jobs[i].p, jobs[i].seed, &jc, b->stream);
         if (rc) {
             free_batch(b);
             return rc;
         }
     }
-    if (cudaMalloc(reinterpret_cast<void **>(&b->d_jobs), sizeof(BatchJob) * n_jobs) != cudaSuccess ||
+    if (alloc_should_fail() ||
+        cudaMalloc(reinterpret_cast<void **>(&b->d_jobs), sizeof(BatchJob) * n_jobs) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&b->d_queue), sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&b->d_iter), sizeof(uint32_t) * n_jobs) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&b->d_active), sizeof(int) * n_jobs) != cudaSuccess ||
@@ -548,6 +556,7 @@ int begin_iterations(muca_batch *b, int n_sweeps)
 
 int muca_batch_iterate(muca_batch *b, int n_iterations, int n_sweeps, int use_graph)
 {
+    MUCA_RANGE("muca_batch_iterate");
     if (!b) return fail(MUCA_ERR_ARG, "null batch");
     if (n_iterations < 1 || n_sweeps < 1) return fail(MUCA_ERR_ARG, "need n_iterations >= 1 and n_sweeps >= 1");
     int rc0 = begin_iterations(b, n_sweeps);
@@ -613,6 +622,7 @@ int enqueue_thermalization(muca_batch *b, int n_sweeps)
 
 int muca_batch_converge(muca_batch *b, int n_sweeps, int therm_sweeps, int max_iterations, int *n_iter_out)
 {
+    MUCA_RANGE("muca_batch_converge");
     if (!b) return fail(MUCA_ERR_ARG, "null batch");
     if (n_sweeps < 1 || max_iterations < 1 || therm_sweeps < 0)
         return fail(MUCA_ERR_ARG, "need n_sweeps >= 1, therm_sweeps >= 0 and max_iterations >= 1");
@@ -666,6 +676,7 @@ int muca_batch_converge(muca_batch *b, int n_sweeps, int therm_sweeps, int max_i
 
 int muca_batch_autotune(muca_batch *b, int n_sweeps, const char *cache_path, int chosen[3])
 {
+    MUCA_RANGE("muca_batch_autotune");
     if (!b) return fail(MUCA_ERR_ARG, "null batch");
     if (n_sweeps < 1) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 1");
     std::string path = cache_path ? cache_path : "";

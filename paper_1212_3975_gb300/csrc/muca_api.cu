@@ -2,7 +2,9 @@
 // and the order of kernel launches for each call of the parallel multicanonical
 // method (arXiv:1212.3975).  No arithmetic of the method lives here.
 #include <atomic>
+#include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,6 +32,16 @@ int cuda_fail(cudaError_t e, const char *what)
 
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+bool alloc_should_fail()
+{
+    static std::atomic<long> remaining{[] {
+        const char *v = std::getenv("MUCA_TEST_FAIL_ALLOC");
+        return v ? std::atol(v) : 0L;
+    }()};
+    if (remaining.load() <= 0) return false;
+    return remaining.fetch_sub(1) == 1;
+}
+
 namespace {
 
 bool is_device_ptr(const void *p)
@@ -43,11 +55,25 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Per-iteration metric lines: with MUCA_METRICS_LOG=<path> every weight update appends
+// one JSON line (iteration, sampled bin range, coverage, min/mean and max/mean of H,
+// convergence flag, attempts/ns of the iteration's sweeps by host clock).  The update
+// then synchronises once to read its statistics.
+FILE *metrics_log()
+{
+    static FILE *f = [] {
+        const char *v = std::getenv("MUCA_METRICS_LOG");
+        return v && *v ? std::fopen(v, "a") : (FILE *)nullptr;
+    }();
+    return f;
+}
+
 template <typename T>
 int dalloc(T **p, size_t count, const char *what)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (alloc_should_fail()) return fail(MUCA_ERR_OOM, std::string("device allocation failed (test hook): ") + what);
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -137,7 +163,8 @@ int alloc_buffers(muca_ctx *c)
         cudaGetLastError();
         return fail(MUCA_ERR_CUDA, "reweight scratch initialisation");
     }
-    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_stats), sizeof(muca_iter_stats)) != cudaSuccess) {
+    if (alloc_should_fail() ||
+        cudaMallocHost(reinterpret_cast<void **>(&c->h_stats), sizeof(muca_iter_stats)) != cudaSuccess) {
         cudaGetLastError();
         return fail(MUCA_ERR_OOM, "pinned allocation failed");
     }
@@ -173,6 +200,7 @@ uint64_t muca_kernel_launches(void) { return g_launches.load(); }
 int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, const muca_config *cfg,
               void *cuda_stream)
 {
+    MUCA_RANGE("muca_init");
     if (!out) return fail(MUCA_ERR_ARG, "out is null");
     *out = nullptr;
     if (model == MUCA_ISING) {
@@ -229,7 +257,14 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
     }
     c->row_words = model == MUCA_ISING ? (L + 31) / 32 : (L + 3) / 4;
     c->lat_words = L * c->row_words;
-    c->p_pad = (p + 31) / 32 * 32;
+    // Fewer groups of 32 chains than SMs: the warp-specialised kernels (L % 4 == 0,
+    // energy ensemble, automatic block size) spread the chains over every SM, cpg per
+    // block.  A chain's attempts are sequential, so at small p the chains' own latency
+    // bounds the rate, and fewer chains per SM contend less for its shared memory.
+    c->cpg = 32;
+    if (L % 4 == 0 && c0.ensemble == MUCA_ENSEMBLE_ENERGY && c0.chains_per_block == 0 && (p + 31) / 32 < c->n_sm)
+        c->cpg = (p + c->n_sm - 1) / c->n_sm;
+    c->p_pad = (p + c->cpg - 1) / c->cpg * 32;
     int rc = alloc_buffers(c);
     if (rc) {
         free_ctx(c);
@@ -273,6 +308,7 @@ int muca_destroy(muca_ctx *ctx)
 
 int muca_reset(muca_ctx *ctx, uint64_t seed)
 {
+    MUCA_RANGE("muca_reset");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if ((seed >> 32) >= (1ull << 30)) return fail(MUCA_ERR_ARG, "seed >> 32 must be < 2^30");
@@ -302,9 +338,15 @@ int muca_sweep_plan(const muca_ctx *ctx)
 
 int muca_iterate(muca_ctx *ctx, int n_sweeps, uint64_t *H_out)
 {
+    MUCA_RANGE("muca_iterate");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (n_sweeps < 1) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 1");
+    if (metrics_log()) {
+        MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        ctx->it_t0 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+        ctx->it_attempts = (double)n_sweeps * ctx->V * ctx->p;
+    }
     MUCA_CUDA_TRY(cudaMemsetAsync(ctx->d_H, 0, sizeof(uint64_t) * ctx->n_bins, ctx->stream));
     if ((rc = launch_sweeps(ctx, kPhaseIterate, n_sweeps, 0u, ctx->iteration, true, nullptr, nullptr, false)))
         return rc;
@@ -315,17 +357,32 @@ int muca_iterate(muca_ctx *ctx, int n_sweeps, uint64_t *H_out)
 
 int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out)
 {
+    MUCA_RANGE("muca_update_weights");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (!ctx->have_hist) return fail(MUCA_ERR_STATE, "no histogram since the last update");
     if ((rc = launch_update(ctx))) return rc;
     ctx->have_hist = 0;
     ctx->lnw_version += 1;
-    if (out) {
+    FILE *log = metrics_log();
+    if (out || log) {
         MUCA_CUDA_TRY(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(muca_iter_stats), cudaMemcpyDeviceToHost,
                                       ctx->stream));
         MUCA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-        *out = *ctx->h_stats;
+        if (out) *out = *ctx->h_stats;
+    }
+    if (log) {
+        const muca_iter_stats &st = *ctx->h_stats;
+        const double t1 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+        const double rate = ctx->it_t0 > 0 && t1 > ctx->it_t0 ? ctx->it_attempts / ((t1 - ctx->it_t0) * 1e9) : 0.0;
+        std::fprintf(log,
+                     "{\"ctx\": \"%p\", \"iteration\": %u, \"lo\": %d, \"hi\": %d, \"n_sampled\": %lld, "
+                     "\"covered\": %d, \"flat\": %d, \"min_over_mean\": %.6g, \"max_over_mean\": %.6g, "
+                     "\"total\": %llu, \"attempts_per_ns\": %.6g}\n",
+                     (void *)ctx, ctx->iteration, st.lo, st.hi, (long long)st.n_sampled, st.covered, st.flat,
+                     st.min_over_mean, st.max_over_mean, (unsigned long long)st.total, rate);
+        std::fflush(log);
+        ctx->it_t0 = 0.0;
     }
     return MUCA_OK;
 }
@@ -333,6 +390,7 @@ int muca_update_weights(muca_ctx *ctx, muca_iter_stats *out)
 int muca_converge(muca_ctx *ctx, int n_sweeps, int therm_sweeps, int max_iterations, int *n_iter_out,
                   muca_iter_stats *last)
 {
+    MUCA_RANGE("muca_converge");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (n_sweeps < 1 || max_iterations < 1 || therm_sweeps < 0)
@@ -356,6 +414,7 @@ int muca_converge(muca_ctx *ctx, int n_sweeps, int therm_sweeps, int max_iterati
 
 int muca_thermalize(muca_ctx *ctx, int n_sweeps)
 {
+    MUCA_RANGE("muca_thermalize");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (n_sweeps < 0) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 0");
@@ -377,6 +436,7 @@ int muca_reset_samples(muca_ctx *ctx)
 
 int muca_set_samples(muca_ctx *ctx, const uint64_t *n, const uint64_t *sum_abs_m, const uint64_t *sum_m2)
 {
+    MUCA_RANGE("muca_set_samples");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (ctx->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
@@ -395,6 +455,7 @@ int muca_set_samples(muca_ctx *ctx, const uint64_t *n, const uint64_t *sum_abs_m
 
 int muca_produce(muca_ctx *ctx, int n_sweeps, int32_t *E_out, int32_t *M_out)
 {
+    MUCA_RANGE("muca_produce");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (n_sweeps < 1) return fail(MUCA_ERR_ARG, "n_sweeps must be >= 1");
@@ -439,6 +500,7 @@ int muca_produce(muca_ctx *ctx, int n_sweeps, int32_t *E_out, int32_t *M_out)
 int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision, double *e, double *C,
                   double *absm, double *chi)
 {
+    MUCA_RANGE("muca_reweight");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (ctx->cfg.ensemble != MUCA_ENSEMBLE_ENERGY)
@@ -488,6 +550,7 @@ int muca_get_lnw(muca_ctx *ctx, double *lnw)
 
 int muca_set_lnw(muca_ctx *ctx, const double *lnw)
 {
+    MUCA_RANGE("muca_set_lnw");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (!lnw) return fail(MUCA_ERR_ARG, "null buffer");
@@ -506,6 +569,7 @@ int muca_get_thresholds(muca_ctx *ctx, uint32_t *thr)
 
 int muca_set_thresholds(muca_ctx *ctx, const uint32_t *thr)
 {
+    MUCA_RANGE("muca_set_thresholds");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (!thr) return fail(MUCA_ERR_ARG, "null buffer");
@@ -599,6 +663,7 @@ std::vector<Blob> blobs(muca_ctx *c)
 
 int muca_save(muca_ctx *ctx, const char *path)
 {
+    MUCA_RANGE("muca_save");
     int rc;
     if ((rc = check_ctx(ctx))) return rc;
     if (!path) return fail(MUCA_ERR_ARG, "null path");
@@ -639,6 +704,7 @@ int muca_save(muca_ctx *ctx, const char *path)
 
 int muca_load(muca_ctx **out, const char *path, void *cuda_stream)
 {
+    MUCA_RANGE("muca_load");
     if (!out || !path) return fail(MUCA_ERR_ARG, "null argument");
     *out = nullptr;
     FILE *f = std::fopen(path, "rb");

@@ -7,10 +7,14 @@
 //   Potts: one byte per site, byte j of word w of row y holds site x = 4 w + j;
 //          row_words = ceil(L / 4).
 //   word k = y * row_words + w of chain c lives at lat[k * p_pad + c].
-// p_pad = p rounded up to a multiple of 32; padding chains are never touched.
+// The warp-specialised sweep kernels give each block a group of cpg <= 32 chains (fewer
+// than 32 when there are fewer than 32 chains per SM, so that every SM runs some):
+// p_pad = ceil(p / cpg) * 32, lanes beyond cpg work on padding columns past
+// ceil(p / cpg) * cpg, and padding chains are never read back.
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string>
 
@@ -86,6 +90,7 @@ struct SweepArgs {
     int32_t *M_rec;
     uint64_t *samples;    // [3][n_bins] production sums (n, sum|M|, sum M^2) or null
     int L, q, p, p_pad, row_words, lat_words, n_bins;
+    int cpg;              // chains per block of the warp-specialised bodies (<= 32)
     int n_sweeps;
     uint32_t sweep0;      // counter word 1 of the first sweep
     uint32_t iteration;   // counter word 2
@@ -134,6 +139,7 @@ struct muca_ctx {
     muca_config cfg;
     cudaStream_t stream;
     int device;
+    int cpg;                  // chains per group of the warp-specialised sweep kernels (<= 32)
     int n_sm;                 // streaming multiprocessors of the device (queried at init)
     int smem_per_sm;          // shared memory per SM and reserved per block (bytes, queried)
     int smem_reserved;
@@ -167,6 +173,8 @@ struct muca_ctx {
     int have_hist;
     int samples_active;
     uint64_t lnw_version, samples_lnw_version;
+    // metric log: host clock at the start of the last iteration's sweeps, its attempts
+    double it_t0, it_attempts;
 };
 
 namespace muca {
@@ -175,6 +183,21 @@ namespace muca {
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 void note_launches(uint64_t n);
+
+// NVTX range around an entry point (visible in profilers; free without one attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define MUCA_RANGE(name) ::muca::NvtxRange muca_range_(name)
+
+// Test hook: with the environment variable MUCA_TEST_FAIL_ALLOC=k the k-th allocation
+// of the process (device or pinned host memory, counting from 1) fails as if no memory
+// were left, so that the clean-up of every allocation path can be tested without a GPU
+// fault.
+bool alloc_should_fail();
 
 #define MUCA_CUDA_TRY(call)                                           \
     do {                                                              \

@@ -458,7 +458,8 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
     const size_t cap = (size_t)kMaxSmem - (ws ? ws_extra_smem(ctx->model) : 0);
     const int width = fast ? (ctx->model == MUCA_ISING ? 5 : 9) : ctx->n_de;
     const size_t table = ((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15;
-    const size_t hist = ((size_t)ctx->n_bins * 4 + 15) & ~(size_t)15;
+    // (+ one slot per lane for the inactive lanes of the warp-specialised kernels)
+    const size_t hist = (((size_t)ctx->n_bins * 4 + 15) & ~(size_t)15) + 128;
     const size_t lat = (size_t)ctx->lat_words * 4 * cpb;
     size_t used = 0;
     pl.table_smem = table <= 96 * 1024;
@@ -471,7 +472,7 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
     // warp-specialised launches: the histogram of attempt pairs (one count per bin
     // change of a single attempt: 5 for Ising, 9 for Potts) when it fits beside the
     // table and the lattices
-    const size_t pairs = ((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15;
+    const size_t pairs = (((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15) + 128;
     pl.hist_pairs = allow_pairs && ws && pl.table_smem && pl.hist_smem && pl.lattice_smem && used - hist + pairs <= cap;
     if (pl.hist_pairs) used += pairs - hist;
     pl.smem_bytes = used;
@@ -529,6 +530,7 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
     a.q = ctx->q;
     a.p = ctx->p;
     a.p_pad = ctx->p_pad;
+    a.cpg = ctx->cpg;
     a.row_words = ctx->row_words;
     a.lat_words = ctx->lat_words;
     a.n_bins = ctx->n_bins;
@@ -537,7 +539,8 @@ int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, 
     a.key0 = (uint32_t)ctx->seed;
     a.rec_stride = ctx->p;
     const int cpb = pl.chains_per_block;
-    const int blocks = (ctx->p + cpb - 1) / cpb;
+    // warp-specialised kernels: one block per group of cpg chains
+    const int blocks = pl.warp_specialized ? (ctx->p + ctx->cpg - 1) / ctx->cpg : (ctx->p + cpb - 1) / cpb;
     // keep every uint32 run length and block-histogram entry below 2^31
     const uint64_t per_sweep = (uint64_t)cpb * ctx->V;
     const int chunk = (int)std::max<uint64_t>(1, std::min<uint64_t>((1ull << 31) / per_sweep, 1u << 30));

@@ -34,6 +34,7 @@ namespace ws {
 constexpr int kRingU = 4;   // slots of Philox draws (one row word each)
 constexpr int kRingS = 3;   // slots of bookkeeping snapshots
 constexpr int kCompactRing = 3;  // draw-ring slots of the compact Ising staging
+constexpr int kHistDummy = 32;   // histogram slots of inactive lanes (one per lane)
 constexpr int kBarFullU = 1, kBarEmptyU = kBarFullU + kRingU;      // ids 1..8
 constexpr int kBarFullS = kBarEmptyU + kRingU, kBarEmptyS = kBarFullS + kRingS;  // ids 9..14
 static_assert(kBarEmptyS + kRingS <= 16, "named barrier ids");
@@ -310,14 +311,22 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     uint32_t *s_tab = smem;
     const int n_hist = HPAIR ? a.n_bins * 5 : a.n_bins;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
-    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) : 0);
+    // the histogram is followed by one slot per lane (kHistDummy) for inactive lanes
+    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) + kHistDummy : 0);
     static_assert(RU >= 2 && RU <= kRingU, "draw ring slots");
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [RU][8][32]
     Snap *s_snap = reinterpret_cast<Snap *>(s_ring + RU * 8 * 32);                       // [kRingS][32]
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int c = cblk * 32 + lane;
-    const bool active = c < a.p;
+    // chain of this lane: group cblk holds chains cblk * cpg ..; lanes beyond cpg take
+    // padding columns after the last group (never read back)
+    const int cpg = a.cpg;
+    const int c = lane < cpg ? cblk * cpg + lane : (a.p_pad >> 5) * cpg + cblk * (32 - cpg) + (lane - cpg);
+    const bool active = lane < cpg && c < a.p;
+    // inactive lanes add their histogram counts into a slot of their own past the
+    // histogram, so that every histogram atomic is a full-warp one (a red.shared issued
+    // by part of a warp only is far slower)
+    uint32_t *const s_hdummy = s_hist + ((n_hist + 3) & ~3) + lane;
     // Roles: 0 decider, 1..NP producers, NP+1 bookkeeper.  A warp issues on the SM
     // sub-partition of its warp slot mod 4, and a block's four warps take the four slots
     // of one aligned group, one per sub-partition.  In the compact staging two blocks
@@ -622,18 +631,15 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                         const int nneq = (int)(((sn.lo >> j) & 1u) + 2u * ((sn.hi >> j) & 1u) + ((qn >> j) & 1u));
                         const bool acc = (sn.flip >> j) & 1u;
                         bin += acc ? 2 - nneq : 0;
-                        if (HIST && active) {
-                            if (HSMEM) {
-                                red_shared(s_hist + bin, 1u);
-                            } else {
-                                if (bin != run_bin) {
-                                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]),
-                                              (unsigned long long)run);
-                                    run_bin = bin;
-                                    run = 0;
-                                }
-                                ++run;
+                        if (HIST && HSMEM) {
+                            red_shared(active ? s_hist + bin : s_hdummy, 1u);
+                        } else if (HIST && active) {
+                            if (bin != run_bin) {
+                                atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
+                                run_bin = bin;
+                                run = 0;
                             }
+                            ++run;
                         }
                     };
                     if (HPAIR) {
@@ -646,7 +652,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                         auto book_pair = [&](int j) {
                             bin += delta(j);
                             const int d = delta(j + 1);
-                            if (active) red_shared(s_hist + 5 * bin + 2 + d, 1u);
+                            red_shared(active ? s_hist + 5 * bin + 2 + d : s_hdummy, 1u);
                             bin += d;
                         };
                         if (nb == 32) {
@@ -790,14 +796,18 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     uint32_t *s_tab = smem;
     const int n_hist = HPAIR ? a.n_bins * 9 : a.n_bins;
     uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
-    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) : 0);
+    // the histogram is followed by one slot per lane (kHistDummy) for inactive lanes
+    uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) + kHistDummy : 0);
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][8 words][2][32]
     uint4 *s_psnap = s_ring + kPottsRing * 16 * 32;                                      // [kRingS][2][32]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vw = BOOKW ? (warp == 0 ? 1 : warp == 1 ? 0 : warp) : warp;  // role: 0 decider, 1..3 producers, 4 bookkeeper
-    const int c = cblk * 32 + lane;
-    const bool active = c < a.p;
+    // chain of this lane (groups of cpg chains; lanes beyond cpg on padding columns)
+    const int cpg = a.cpg;
+    const int c = lane < cpg ? cblk * cpg + lane : (a.p_pad >> 5) * cpg + cblk * (32 - cpg) + (lane - cpg);
+    const bool active = lane < cpg && c < a.p;
+    uint32_t *const s_hdummy = s_hist + ((n_hist + 3) & ~3) + lane;  // inactive lanes' histogram slot
 
     if (TSMEM)
         for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
@@ -1021,7 +1031,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
                 if (HIST && !BOOKW) {
                     const int bin = bin_of(Pa);
                     if (HSMEM) {
-                        if (active) red_shared(s_hist + bin, 1u);
+                        red_shared(active ? s_hist + bin : s_hdummy, 1u);
                     } else {
                         if (bin != run_bin) {
                             if (active)
@@ -1120,16 +1130,14 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             if (HPAIR) {
                 // one count per pair of attempts: (0, 1) and (2, 3)
                 const int b0 = bin_of(pb.x), b1 = bin_of(pb.y), b2 = bin_of(pb.z), b3 = bin_of(pb.w);
-                if (active) {
-                    red_shared(s_hist + 9 * b0 + 4 + (b1 - b0), 1u);
-                    red_shared(s_hist + 9 * b2 + 4 + (b3 - b2), 1u);
-                }
+                red_shared(active ? s_hist + 9 * b0 + 4 + (b1 - b0) : s_hdummy, 1u);
+                red_shared(active ? s_hist + 9 * b2 + 4 + (b3 - b2) : s_hdummy, 1u);
             } else if (HIST) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int bin = bin_of(k == 0 ? pb.x : k == 1 ? pb.y : k == 2 ? pb.z : pb.w);
                     if (HSMEM) {
-                        if (active) red_shared(s_hist + bin, 1u);
+                        red_shared(active ? s_hist + bin : s_hdummy, 1u);
                     } else {
                         if (bin != run_bin) {
                             if (active)

@@ -167,10 +167,10 @@ def fit_inverse_l(L_list, values):
 
 
 def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, production=4000,
-                  beta_range=(1.25, 1.45), seed0=3):
+                  beta_range=(1.25, 1.45), seed0=3, m_factor=1.0):
     """Order-disorder interface tension of the 8-state Potts model (Sec. 5) for every L:
     `runs` independent MUCA runs of p chains each, iterated to convergence together
-    (muca_batch_converge at M = Eq. 7's M_opt(L, p)); every converged run is thermalised,
+    (muca_batch_converge at M = m_factor x Eq. 7's M_opt(L, p)); every converged run is thermalised,
     runs a production that keeps only the per-bin sums, and gives sigma_od(L) from the
     equal-height analysis of muca_interface_tension.  sigma_od(L) is the mean over the
     converged runs; finally sigma_od(L) = sigma_inf + c/L is fitted.
@@ -180,7 +180,7 @@ def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, pr
     from . import check, lib
     out = {}
     for L in L_list:
-        M = max(10, int(round(eq7_m_opt(POTTS, L, p))))
+        M = max(10, int(round(m_factor * eq7_m_opt(POTTS, L, p))))
         jobs = [(POTTS, L, 8, p, seed0 + 100 * L + r) for r in range(runs)]
         b = MucaBatch(jobs)
         try:
@@ -208,3 +208,52 @@ def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, pr
     Ls = [L for L in out if math.isfinite(out[L]["sigma_od"])]
     fit = fit_inverse_l(Ls, [out[L]["sigma_od"] for L in Ls]) if len(Ls) >= 3 else (math.nan, math.nan)
     return out, fit
+
+
+def eq7_scan(model, L_list, p_list, M_factors, seeds, max_iterations):
+    """Sec. 4 / Eq. 7 from scratch: an M scan at every L, M_opt(L, p) from its minima,
+    M_1(L) from M_opt(L, p) = M_1 / p, and (a, b) of M_1(L) = a L^(2+b)."""
+    per_L = {}
+    for L in L_list:
+        scan = m_scan(model, L, p_list, M_factors, seeds, max_iterations)
+        m_opt, per_chain, S = speedup_from_scan(scan)
+        per_L[int(L)] = {"M_opt": {int(p): m_opt[p] for p in p_list}, "M1": fit_m1(p_list, [m_opt[p] for p in p_list]),
+                         "S_star": {int(p): S.get(p, math.nan) for p in p_list}}
+    Ls = [L for L in per_L if math.isfinite(per_L[L]["M1"])]
+    ab = fit_power(Ls, [per_L[L]["M1"] for L in Ls]) if len(Ls) >= 2 else (math.nan, math.nan)
+    return per_L, ab
+
+
+def main(argv=None):
+    """Command line of the longer study runs (their results are quoted in the design
+    notes):  python -m paper_1212_3975_gb300.study sigma|eq7 [options]; prints JSON."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["sigma", "eq7"])
+    ap.add_argument("--L", type=int, nargs="+", required=True)
+    ap.add_argument("--p", type=int, nargs="+", default=[16])
+    ap.add_argument("--runs", type=int, default=4, help="sigma: independent runs per L")
+    ap.add_argument("--seeds", type=int, default=10, help="eq7: seeds per (p, M)")
+    ap.add_argument("--m-factor", type=float, default=1.0, help="sigma: M = factor x Eq. 7 M_opt(L, p)")
+    ap.add_argument("--factors", type=float, nargs="+", default=[0.5, 0.7, 1.0, 1.4, 2.0, 2.8, 4.0])
+    ap.add_argument("--max-iterations", type=int, default=300)
+    ap.add_argument("--production", type=int, default=4000)
+    ap.add_argument("--model", choices=["ising", "potts"], default="ising")
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    if a.what == "sigma":
+        res, (s_inf, c) = sigma_od_scan(a.L, p=a.p[0], runs=a.runs, max_iterations=a.max_iterations,
+                                        production=a.production, m_factor=a.m_factor)
+        out = {"per_L": res, "sigma_inf": s_inf, "c": c}
+    else:
+        model = ISING if a.model == "ising" else POTTS
+        per_L, (aa, bb) = eq7_scan(model, a.L, a.p, a.factors, a.seeds, a.max_iterations)
+        out = {"per_L": per_L, "a": aa, "b": bb, "eq7": EQ7[model]}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    print(json.dumps(out, default=lambda x: None if isinstance(x, float) and not math.isfinite(x) else x))
+
+
+if __name__ == "__main__":
+    main()
