@@ -59,6 +59,10 @@ COUNTERS = {
     # profiles/ising_ws_compact_L64_p9728.md
     "ising_L64_compact": {"source": "7239a44f398aea87", "inst_per_attempt": 1.956,
                           "shared_wavefronts_per_attempt": 0.381, "traffic_bytes_per_launch": 5170},
+    # Ising 64x64, compact staging with the 16-bit table, three blocks per SM
+    # (p = 14592): profiles/ising_ws_t16_L64_p14592.md
+    "ising_L64_t16": {"source": "610fd672c5d9f3bc", "inst_per_attempt": 1.971,
+                      "shared_wavefronts_per_attempt": 0.372, "traffic_bytes_per_launch": 7665408},
     # 8-Potts 32x32 (p = 4096): profiles/potts_ws_sweep_L32_p4096.md
     "potts_L32": {"source": "7239a44f398aea87", "inst_per_attempt": 3.441, "shared_wavefronts_per_attempt": 0.521,
                   "traffic_bytes_per_launch": 4321792},
@@ -381,14 +385,16 @@ def sweep_roofline(w, sweep_avg_ms, n_sm, sm_max):
     }
 
 
-def p_sweep(m, torch, stream, n_sm, sm_max, sweeps=100):
+def p_sweep(m, torch, stream, n_sm, sm_max):
     """Ising 64x64 weight-iteration launches at growing p: where the issue roofline
     saturates.  One block of 32 chains per SM up to p = 32 x SMs; beyond, the compact
-    staging runs two blocks per SM."""
+    staging runs two blocks per SM, and three (the table of 16-bit threshold halves)
+    where that takes fewer waves: at 96 and 192 x SMs."""
     timed = cuda_timer(torch, stream)
     peak = n_sm * 4 * sm_max * 1e6 / 1e9
     out = []
-    for p in (1024, 2048, 32 * n_sm, 64 * n_sm, 128 * n_sm):
+    for p in (1024, 2048, 32 * n_sm, 64 * n_sm, 96 * n_sm, 128 * n_sm, 192 * n_sm):
+        sweeps = 100 if p <= 96 * n_sm else 50
         g = m.Muca(m.MUCA_ISING, 64, 2, p, 1, stream=stream.cuda_stream)
         g.iterate(2)
         g.update_weights()
@@ -398,9 +404,11 @@ def p_sweep(m, torch, stream, n_sm, sm_max, sweeps=100):
         t = min(timed(lambda: m.check(m.lib().muca_iterate(g.handle, sweeps, None))) for _ in range(2))
         g.close()
         rate = p * 4096 * sweeps / t / 1e9
-        c = counters("ising_L64_compact" if plan & m.MUCA_PLAN_COMPACT else "ising_L64")
+        c = counters("ising_L64_t16" if plan & m.MUCA_PLAN_TABLE16 else
+                     "ising_L64_compact" if plan & m.MUCA_PLAN_COMPACT else "ising_L64")
         ok = c["matches_source"]
         out.append({"p": p, "attempts_per_ns": rnd(rate), "compact": bool(plan & m.MUCA_PLAN_COMPACT),
+                    "blocks_per_sm": 3 if plan & m.MUCA_PLAN_TABLE16 else 2 if plan & m.MUCA_PLAN_COMPACT else 1,
                     "issue_frac": rnd(rate * c["inst_per_attempt"] / peak, 3) if ok else None,
                     "lsu_frac": rnd(rate * c["shared_wavefronts_per_attempt"] / (n_sm * sm_max * 1e-3), 3)
                     if ok else None,

@@ -252,7 +252,12 @@ int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
  *  MUCA_PLAN_PAIR_HIST      histogram of pairs of consecutive attempts,
  *  MUCA_PLAN_COMPACT        compact staging, two blocks per SM (more groups of 32
  *                           chains than SMs),
- *  MUCA_PLAN_WARP_SPECIALIZED  decider / producer / bookkeeper warps (L % 4 == 0).
+ *  MUCA_PLAN_WARP_SPECIALIZED  decider / producer / bookkeeper warps (L % 4 == 0),
+ *  MUCA_PLAN_TABLE16        compact staging with the upper 16 bits of the thresholds
+ *                           in shared memory, three blocks per SM (Ising, L % 32 == 0,
+ *                           L >= 64, more than two groups of 32 chains per SM); a
+ *                           draw whose upper half ties the table entry replays its
+ *                           word from the 32-bit table, so results are unchanged.
  * Errors: MUCA_ERR_ARG (null context). */
 #define MUCA_PLAN_LATTICE_SMEM 1
 #define MUCA_PLAN_HIST_SMEM 2
@@ -260,6 +265,7 @@ int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
 #define MUCA_PLAN_PAIR_HIST 8
 #define MUCA_PLAN_COMPACT 16
 #define MUCA_PLAN_WARP_SPECIALIZED 32
+#define MUCA_PLAN_TABLE16 64
 int muca_sweep_plan(const muca_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

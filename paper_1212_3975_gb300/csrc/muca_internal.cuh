@@ -105,6 +105,7 @@ struct SweepPlan {
     bool hist_pairs;        // warp-specialised: shared histogram of attempt pairs
     bool warp_specialized;  // decider / producer / bookkeeper warps per 32 chains
     bool compact;           // warp-specialised Ising: two blocks per SM (3-slot draw ring)
+    bool t16;               // compact with a table of 16-bit threshold halves: three blocks per SM
     int chains_per_block;
     size_t smem_bytes;      // staging of the plan (table, histogram, lattices)
 };

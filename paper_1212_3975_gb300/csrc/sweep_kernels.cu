@@ -441,6 +441,7 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
 {
     SweepPlan pl;
     pl.compact = false;
+    pl.t16 = false;
     int cpb = ctx->cfg.chains_per_block;
     if (cpb <= 0) {
         // Spread the chains over the SMs: one warp per block while that leaves SMs
@@ -493,6 +494,25 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
             pl.hist_pairs = false;
             pl.smem_bytes = table + hist;
         }
+        // More groups than two per SM, and rows of whole words (at least two: the
+        // stream decider): the table of the upper 16-bit halves of the thresholds (ties
+        // replayed from the 32-bit table) fits a third block per SM.  A block of three
+        // per SM takes about 1.26 times as long as one of two per SM (measured at
+        // 64 x 64), so three per SM pays when it needs enough fewer waves: at 3 or 6
+        // groups per SM, not at 4.
+        const size_t table16 = ((size_t)ctx->n_bins * 5 * 2 + 15) & ~(size_t)15;
+        const size_t comp16 = table16 + hist + ws_extra_smem(ctx->model, true);
+        const long groups = ctx->p_pad / 32, n_sm = ctx->n_sm;
+        const long waves2 = (groups + 2 * n_sm - 1) / (2 * n_sm), waves3 = (groups + 3 * n_sm - 1) / (3 * n_sm);
+        if (ctx->L % 32 == 0 && ctx->L >= 64 && groups > 2 * n_sm && 126 * waves3 <= 100 * waves2 &&
+            3 * (comp16 + reserved) <= per_sm) {
+            pl.compact = true;
+            pl.t16 = true;
+            pl.hist_smem = true;
+            pl.lattice_smem = false;
+            pl.hist_pairs = false;
+            pl.smem_bytes = table16 + hist;
+        }
     }
     return pl;
 }
@@ -501,7 +521,8 @@ int plan_flags(const SweepPlan &pl)
 {
     return (pl.lattice_smem ? MUCA_PLAN_LATTICE_SMEM : 0) | (pl.hist_smem ? MUCA_PLAN_HIST_SMEM : 0) |
            (pl.table_smem ? MUCA_PLAN_TABLE_SMEM : 0) | (pl.hist_pairs ? MUCA_PLAN_PAIR_HIST : 0) |
-           (pl.compact ? MUCA_PLAN_COMPACT : 0) | (pl.warp_specialized ? MUCA_PLAN_WARP_SPECIALIZED : 0);
+           (pl.compact ? MUCA_PLAN_COMPACT : 0) | (pl.warp_specialized ? MUCA_PLAN_WARP_SPECIALIZED : 0) |
+           (pl.t16 ? MUCA_PLAN_TABLE16 : 0);
 }
 
 int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,

@@ -5,11 +5,11 @@ namespace muca {
 namespace {
 using namespace ws;
 
-template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU>
-__global__ void __launch_bounds__(128, 1) ising_ws_kernel(SweepArgs a)
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU, bool T16>
+__global__ void __launch_bounds__(128, T16 ? 3 : 1) ising_ws_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    ising_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM, RU>(a, blockIdx.x, smem);
+    ising_ws_body<HIST, RECORD, TSMEM, HMODE, LSMEM, RU, T16>(a, blockIdx.x, smem);
 }
 
 // iteration and production launches: five warps (decider, 3 producers, bookkeeper)
@@ -22,17 +22,17 @@ __global__ void __launch_bounds__(160) potts_ws_kernel(SweepArgs a)
 
 // HMODE: histogram in global memory (0), shared per attempt (1), shared per pair of
 // attempts (2)
-template <int MODEL, bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU = kRingU>
+template <int MODEL, bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU = kRingU, bool T16 = false>
 cudaError_t launch_ws(const SweepArgs &a, int blocks, size_t smem, cudaStream_t st)
 {
-    auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM, RU>
+    auto kern = MODEL == MUCA_ISING ? ising_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM, RU, T16>
                                     : potts_ws_kernel<HIST, RECORD, TSMEM, HMODE, LSMEM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (RU != kRingU) {
-        // compact staging: the whole carve-out as shared memory, so two blocks fit
+        // compact staging: the whole carve-out as shared memory, so two (three) blocks fit
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                              cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
@@ -48,7 +48,10 @@ cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size
     if (HIST && pl.hist_smem && pl.hist_pairs)
         return launch_ws<MODEL, HIST, RECORD, true, 2, true>(a, blocks, smem, st);
     // compact Ising staging (two blocks per SM): table and histogram in shared memory,
-    // lattices in global memory, three draw-ring slots
+    // lattices in global memory, three draw-ring slots; with the table of 16-bit
+    // threshold halves three blocks per SM
+    if (MODEL == MUCA_ISING && pl.compact && pl.t16)
+        return launch_ws<MODEL, HIST, RECORD, true, HIST ? 1 : 0, false, kCompactRing, true>(a, blocks, smem, st);
     if (MODEL == MUCA_ISING && pl.compact)
         return launch_ws<MODEL, HIST, RECORD, true, HIST ? 1 : 0, false, kCompactRing>(a, blocks, smem, st);
     const int key = (pl.table_smem ? 4 : 0) | ((HIST && pl.hist_smem) ? 2 : 0) | (pl.lattice_smem ? 1 : 0);

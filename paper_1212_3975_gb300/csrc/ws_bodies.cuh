@@ -58,6 +58,12 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t saddr)
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
     return v;
 }
+__device__ __forceinline__ uint32_t lds_u16(uint32_t saddr)
+{
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(saddr));
+    return v;
+}
 __device__ __forceinline__ uint32_t ldg_nc_u32(const uint32_t *p)
 {
     uint32_t v;
@@ -145,6 +151,22 @@ __device__ __forceinline__ Quad site_quad(const WordCtx &x, int g, bool rowstart
     return r;
 }
 
+// The same constants for the table of 16-bit entries (threshold upper halves): offsets
+// 2 n0 / 2 n1 and bin changes 20 - 10 n (10 bytes per bin row).
+__device__ __forceinline__ Quad site_quad16(const WordCtx &x, int g, bool rowstart)
+{
+    const uint32_t pre2 = spread4(x.lo, g, 1) + spread4(x.hi, g, 2);  // 2 x (up + down + right)
+    const uint32_t q2 = spread4(x.qw, g, 1);
+    Quad r;
+    r.K0 = pre2 + q2;
+    r.K1 = pre2 + 0x02020202u - q2;
+    if (rowstart) r.K1 = (r.K1 & 0xFFFFFF00u) | (r.K0 & 0xFFu);
+    // per byte 148 - 5 K >= 108: no borrow; xor 0x80 recentres to 20 - 10 n
+    r.D0 = (0x94949494u - 5u * r.K0) ^ 0x80808080u;
+    r.D1 = (0x94949494u - 5u * r.K1) ^ 0x80808080u;
+    return r;
+}
+
 // Ising decider for rows of whole words (L % 32 == 0, at least two words per row).
 // The sites of consecutive words form one software pipeline: while word it is decided,
 // the lattice words and neighbour planes of word it+1 are prepared, its first draws
@@ -157,20 +179,37 @@ __device__ __forceinline__ Quad site_quad(const WordCtx &x, int g, bool rowstart
 // CTX: site of the current word at which the next word's neighbour planes are formed
 // from its lattice words (loaded at the start of the current word): early when the
 // lattices are in shared memory, later when they come from L2.
-template <bool BOOK, bool TSMEM, int RU, int RS, int CTX>
+//
+// T16: the table in shared memory holds the upper 16 bits of every threshold (10 bytes
+// per bin row), and a site compares the upper 16 bits of its draw with it.  That
+// decides exactly unless the two halves are equal (probability ~2^-16 per attempt), in
+// which case the fast path rejects, which always leaves a valid bin.  A lane that met
+// such a tie marks it, and at the end of the word, if any lane did, the warp replays the
+// word from the state it started it in, reading the 32-bit threshold from global memory
+// where a draw ties its entry, and reloads the next site's candidates: every decision
+// is the exact one.
+// bin20 / d20p are in row bytes: 20 per bin, 10 per bin with T16.
+template <bool BOOK, bool TSMEM, int RU, int RS, int CTX, bool T16 = false>
 __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t *lp, const size_t ls,
                                                     const uint32_t tab_s, const uint4 *s_ring, Snap *s_snap,
                                                     const int NU, const int lane, const int total, uint32_t &bin20,
-                                                    uint32_t &d20p, bool &ap)
+                                                    uint32_t &d20p, bool &ap, const bool active)
 {
 #define LAT(k) lp[(size_t)(k) * ls]
+    static_assert(!T16 || TSMEM, "the 16-bit table lives in shared memory");
     const int L = a.L, RW = a.row_words;
     // (fields of `a` are read once here: in the batched kernel `a` lives in shared memory,
     // and every named barrier would make the compiler read it again)
     const char *const ktab_b = reinterpret_cast<const char *>(a.ktab) - tab_s;
+    const uint32_t *const ktab32 = a.ktab;
     auto tload = [&](uint32_t o) -> uint32_t {
-        return TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(ktab_b + o));
+        return T16 ? lds_u16(o) : TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(ktab_b + o));
     };
+    auto quad = [&](const WordCtx &x, int g, bool rowstart) {
+        return T16 ? site_quad16(x, g, rowstart) : site_quad(x, g, rowstart);
+    };
+    constexpr uint32_t ROW = T16 ? 10u : 20u;  // bytes per bin row
+    bool tie = false;                          // a lane met an undecided 16-bit compare
     auto row_up = [&](int y) { return (y == 0 ? L - 1 : y - 1) * RW; };    // row above: updated
     auto row_down = [&](int y) { return (y == L - 1 ? 0 : y + 1) * RW; };  // row below: old (new for y = L-1)
 
@@ -181,7 +220,7 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
     // P0 / P1: table address of the current site's bin (tab_s + 20 bin) if the previous
     // attempt was rejected / accepted
     uint32_t P0 = tab_s + bin20, P1 = P0 + d20p;
-    Quad q0 = site_quad(cur, 0, true);
+    Quad q0 = quad(cur, 0, true);
     uint32_t A0 = tload(P0 + ubyte(q0.K0, 0)), A1 = tload(P1 + ubyte(q0.K1, 0));
     bar_sync(kBarFullU + 0, NU);
     uint4 blk = s_ring[lane], blk_next = s_ring[32 + lane];
@@ -219,7 +258,9 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
         WordCtx nx;
         uint4 nblk = make_uint4(0u, 0u, 0u, 0u), nblk_next = nblk;
         uint32_t Rw = cur.R;
-        Quad q1 = site_quad(cur, 1, false);  // constants of the next four sites
+        const uint32_t P0s = P0, P1s = P1;  // state at the start of the word (replay)
+        const bool aps = ap;
+        Quad q1 = quad(cur, 1, false);  // constants of the next four sites
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             const int k = j & 3;
@@ -228,9 +269,9 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
                 if (j < 28) blk_next = src[((j >> 2) + 1) * 32];
                 q0 = q1;
                 if (j < 28)
-                    q1 = site_quad(cur, (j >> 2) + 1, false);
+                    q1 = quad(cur, (j >> 2) + 1, false);
                 else
-                    q1 = site_quad(nx, 0, w1 == 0);  // site 0 of the next word
+                    q1 = quad(nx, 0, w1 == 0);  // site 0 of the next word
             }
             if (j == CTX) nx = word_ctx(R1, U1, D1w, Rn1, lb1);
             if (j == 28 && has_next) {
@@ -254,7 +295,14 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
                 A1n = tload(nP1 + K1n);
             }
             const uint32_t A = ap ? A1 : A0;
-            const bool acc = u < A;
+            bool acc;
+            if (T16) {
+                const uint32_t uh = u >> 16;
+                acc = uh < A;
+                tie |= uh == A;
+            } else {
+                acc = u < A;
+            }
             A0 = A0n;
             A1 = A1n;
             P0 = Pc;
@@ -264,6 +312,44 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
             ap = acc;
         }
         q0 = q1;
+        if (T16 && __any_sync(0xffffffffu, tie && active)) {
+            // exact replay of the word from its start: the 16-bit entries decide again,
+            // and a draw that ties its entry reads the 32-bit threshold
+            uint32_t bin = ((aps ? P1s : P0s) - tab_s) / ROW;
+            bool apr = aps;
+            uint32_t Rr = cur.R, b31 = 0u, n31 = 0u;
+            for (int g = 0; g < 8; ++g) {
+                const Quad qq = quad(cur, g, w == 0 && g == 0);
+                const uint4 bl = src[g * 32];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t n = (apr ? ubyte(qq.K1, k) : ubyte(qq.K0, k)) >> 1;
+                    const uint32_t u = k == 0 ? bl.x : k == 1 ? bl.y : k == 2 ? bl.z : bl.w;
+                    const uint32_t uh = u >> 16, Ah = lds_u16(tab_s + ROW * bin + 2u * n);
+                    bool acc = uh < Ah;
+                    if (uh == Ah) acc = u < __ldg(ktab32 + bin * 5u + n);
+                    if (g == 7 && k == 3) {
+                        b31 = bin;
+                        n31 = n;
+                    }
+                    if (acc) {
+                        bin = bin + 2u - n;
+                        Rr ^= 1u << (4 * g + k);
+                    }
+                    if (g == 0 && k == 0 && w == 0) first_new = (cur.R & 1u) ^ (acc ? 1u : 0u);
+                    apr = acc;
+                }
+            }
+            Rw = Rr;
+            ap = apr;
+            P0 = tab_s + ROW * b31;      // bin before site 31
+            P1 = P0 + ROW * (2u - n31);  // ... and after it if it was accepted
+            if (has_next) {              // the next site's candidates
+                A0 = tload(P0 + ubyte(q0.K0, 0));
+                A1 = tload(P1 + ubyte(q0.K1, 0));
+            }
+        }
+        tie = false;
         if (it < total - RU) bar_arrive(kBarEmptyU + slot, NU);
         LAT(y * RW + w) = Rw;
         if (BOOK) {
@@ -296,7 +382,9 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
 // sum_d C[b - d][d + 2].  Mode 2 halves the shared-memory atomics, which otherwise
 // delay the decider's table loads.
 // RU: slots of the draw ring (4; 3 in the compact staging that fits two blocks per SM)
-template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU = kRingU>
+// T16: the shared table holds the upper 16 bits of the thresholds (compact staging of
+// three blocks per SM; rows of whole words, at least two per row: the stream decider)
+template <bool HIST, bool RECORD, bool TSMEM, int HMODE, bool LSMEM, int RU = kRingU, bool T16 = false>
 __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk, uint32_t *smem)
 {
     __syncthreads();  // smem may still be read by a previous work unit of this block
@@ -307,10 +395,13 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     constexpr int NT = 128;                     // decider + producers (+ bookkeeper)
     constexpr int NU = 32 * (1 + NP);           // threads on the draw-ring barriers
     constexpr int BOOK_WARP = 1 + NP;
+    static_assert(!T16 || (TSMEM && !LSMEM && HMODE != 2), "16-bit table: compact staging only");
     const int n_tab = a.n_bins * 5;
+    constexpr uint32_t ROWB = T16 ? 10u : 20u;  // table bytes per bin
     uint32_t *s_tab = smem;
     const int n_hist = HPAIR ? a.n_bins * 5 : a.n_bins;
-    uint32_t *s_hist = smem + (TSMEM ? ((n_tab + 3) & ~3) : 0);
+    const int tab_words = T16 ? (n_tab + 1) >> 1 : n_tab;
+    uint32_t *s_hist = smem + (TSMEM ? ((tab_words + 3) & ~3) : 0);
     // the histogram is followed by one slot per lane (kHistDummy) for inactive lanes
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) + kHistDummy : 0);
     static_assert(RU >= 2 && RU <= kRingU, "draw ring slots");
@@ -337,30 +428,46 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     // the slot order at p = 9728, 64 x 64).  With one block per SM the role is the warp
     // index, read back from shared memory (measured 5% faster at p = 1024 than taking
     // it from the thread index directly: the compiler lays the role branches out
-    // differently).  If a block's four sub-partitions are not distinct the role is the
-    // warp index.
+    // differently).  With three blocks per SM (T16) the block in slot group g puts its
+    // decider on sub-partition g mod 4 and its bookkeeper on (g + 3) mod 4, so that the
+    // three deciders issue from three sub-partitions.  If a block's four sub-partitions
+    // are not distinct the role is the warp index.
     constexpr bool PAIR_ROLES = RU != kRingU;
     __shared__ int s_sub[4], s_par;
     if (lane == 0) {
         uint32_t slot = 0u;
         if (PAIR_ROLES) asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
         s_sub[tid >> 5] = PAIR_ROLES ? (int)(slot & 3u) : (tid >> 5);
-        if (tid == 0) s_par = (int)((slot >> 2) & 1u);
+        if (tid == 0) s_par = (int)((slot >> 2) & (T16 ? 3u : 1u));
     }
     __syncthreads();
     int warp = s_sub[tid >> 5];
     if (PAIR_ROLES) {
         if (((1 << s_sub[0]) | (1 << s_sub[1]) | (1 << s_sub[2]) | (1 << s_sub[3])) == 0xF) {
-            const int dsub = s_par ? 3 : 0;  // the decider's sub-partition
-            // role 3: the bookkeeper (the third producer in launches without one)
-            warp = warp == dsub ? 0 : warp == 3 - dsub ? 3 : warp;
+            // sub-partitions of the decider and of the bookkeeper (role 3: the third
+            // producer in launches without one); the producers take the other two in order
+            const int dsub = T16 ? s_par : s_par ? 3 : 0;
+            const int bsub = T16 ? (s_par + 3) & 3 : 3 - dsub;
+            const int sub = warp;
+            if (sub == dsub) {
+                warp = 0;
+            } else if (sub == bsub) {
+                warp = 3;
+            } else {
+                warp = 1;
+                for (int t = 0; t < sub; ++t) warp += (t != dsub && t != bsub) ? 1 : 0;
+            }
         } else {
             warp = tid >> 5;
         }
     }
 
-    if (TSMEM)
+    if (T16) {
+        uint16_t *s_tab16 = reinterpret_cast<uint16_t *>(s_tab);
+        for (int i = tid; i < n_tab; i += NT) s_tab16[i] = (uint16_t)(a.ktab[i] >> 16);
+    } else if (TSMEM) {
         for (int i = tid; i < n_tab; i += NT) s_tab[i] = a.ktab[i];
+    }
     if (HIST && HSMEM)
         for (int i = tid; i < n_hist; i += NT) s_hist[i] = 0u;
     if (LSMEM && warp == 0)
@@ -427,12 +534,12 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         const char *const ktab_g = reinterpret_cast<const char *>(a.ktab);
 #define TAB_BYTES(o) (TSMEM ? lds_u32(tab_s + (o)) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(ktab_g + (o))))
         const int bin0 = active ? (a.E[c] + 2 * V) >> 2 : (V >> 1);
-        uint32_t bin20 = 20u * (uint32_t)bin0;  // 4*5*bin before the previous decision
-        uint32_t d20p = 0u;                     // its change if the previous attempt was accepted
-        bool ap = false;                        // previous attempt accepted
-        if (last_bits == 32 && RW >= 2) {
-            ising_decide_stream<BOOK, TSMEM, RU, kRingS, LSMEM ? 8 : 20>(a, lp, ls, tab_s, s_ring, s_snap, NU, lane, total, bin20,
-                                                             d20p, ap);
+        uint32_t bin20 = ROWB * (uint32_t)bin0;  // table row of the bin before the previous decision
+        uint32_t d20p = 0u;                      // its change if the previous attempt was accepted
+        bool ap = false;                         // previous attempt accepted
+        if (T16 || (last_bits == 32 && RW >= 2)) {
+            ising_decide_stream<BOOK, TSMEM, RU, kRingS, LSMEM ? 8 : 20, T16>(a, lp, ls, tab_s, s_ring, s_snap, NU, lane,
+                                                                             total, bin20, d20p, ap, active);
         } else {
         int it = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
@@ -597,7 +704,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         }
         if (active && !BOOK) {
             // no bookkeeper: apply the pending decision and recount M
-            const uint32_t bin_end = (ap ? bin20 + d20p : bin20) / 20u;
+            const uint32_t bin_end = (ap ? bin20 + d20p : bin20) / ROWB;
             a.E[c] = 4 * (int)bin_end - 2 * V;
             int up = 0;
             for (int k = 0; k < a.lat_words; ++k) up += __popc(LAT(k));

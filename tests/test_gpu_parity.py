@@ -161,16 +161,18 @@ def test_produce_records_and_samples(muca, model, L, p):
     assert np.array_equal(n, on) and np.array_equal(s1, os1) and np.array_equal(s2, os2)
 
 
-@pytest.mark.parametrize("L", [48, 64])
-def test_compact_staging_bit_exact(muca, L):
+@pytest.mark.parametrize("L,per_sm", [(48, 1), (64, 1), (64, 2)])
+def test_compact_staging_bit_exact(muca, L, per_sm):
     """More groups of 32 chains than SMs: the compact staging (two blocks per SM, the
     table and a histogram of single attempts in shared memory, the lattices in global
-    memory, three draw-ring slots), with a ragged last group.  Every chain runs on both
-    sides with the same tables: iteration histograms, spins, E, M, thermalisation,
-    production records and sums bit for bit."""
+    memory, three draw-ring slots), with a ragged last group; more than two groups per
+    SM at L = 64: three blocks per SM with the table of 16-bit threshold halves, whose
+    ties (about 2^-16 of the attempts, a few thousand here) replay their word from the
+    32-bit table.  Every chain runs on both sides with the same tables: iteration
+    histograms, spins, E, M, thermalisation, production records and sums bit for bit."""
     import torch
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    p = 32 * (n_sm + 2) + 5
+    p = 32 * (per_sm * n_sm + 2) + 5
     seed = 4321
     lnw = random_weights(ISING, L, L + 3, 0.38)
     thr = weights.thresholds(ISING, L, lnw)
@@ -178,6 +180,7 @@ def test_compact_staging_bit_exact(muca, L):
         plan = g.plan()
         assert plan & muca.MUCA_PLAN_COMPACT and plan & muca.MUCA_PLAN_TABLE_SMEM, plan
         assert not plan & muca.MUCA_PLAN_LATTICE_SMEM and not plan & muca.MUCA_PLAN_PAIR_HIST, plan
+        assert bool(plan & muca.MUCA_PLAN_TABLE16) == (per_sm == 2), plan
         g.set_thresholds(thr)
         H1 = g.iterate(2)
         H2 = g.iterate(1)
