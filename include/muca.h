@@ -354,8 +354,16 @@ int muca_interface_tension(muca_ctx *ctx, double beta_lo, double beta_hi, int n_
                            double *beta_eqh, double *ln_ratio, int *peaks);
 
 /* Checkpoint / resume: the complete state (spins, E, M, Potts counts, ln W, the
- * recursion accumulator, thresholds, counters, seed, production sums) in one file.
- * Philox is counter-based, so a resumed run continues bit-identically. */
+ * recursion accumulator, thresholds, counters, seed, production sums) in one file
+ * (format version 3: a header, then the arrays; the per-chain arrays hold the p
+ * chains only, so a file loads on a device of any SM count).  Philox is
+ * counter-based, so a resumed run continues bit-identically.
+ * muca_load: *out = a new context on cuda_stream (NULL: the legacy default stream),
+ * owned by the caller (muca_destroy).  Errors: MUCA_ERR_ARG (null argument),
+ * MUCA_ERR_IO (missing or foreign file, another format version, a truncated file,
+ * spins outside the model, or E / M / counts that are not those of the spins: they
+ * are recounted on the device and compared), MUCA_ERR_OOM / MUCA_ERR_CUDA (device);
+ * on error *out is NULL and nothing is left allocated. */
 int muca_save(muca_ctx *ctx, const char *path);
 int muca_load(muca_ctx **out, const char *path, void *cuda_stream);
 

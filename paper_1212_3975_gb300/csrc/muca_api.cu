@@ -640,24 +640,55 @@ struct CkptHeader {
     uint64_t lnw_version, samples_lnw_version;
 };
 
+// A device array in the file.  Per-chain arrays (rows x p_pad on the device: the
+// chain-interleaved layout, whose padding depends on the device's SM count) are
+// written as rows x p, so that a checkpoint loads on any device.
 struct Blob {
     void *dev;
-    size_t bytes;
+    size_t elem, rows;  // element bytes; rows of p_pad (per chain) or one row of `n`
+    size_t n;           // elements of a non-chain array (0: per chain)
+    size_t file_bytes(const muca_ctx *c) const { return elem * (n ? n : rows * (size_t)c->p); }
 };
 
 std::vector<Blob> blobs(muca_ctx *c)
 {
     const size_t nb = c->n_bins;
-    return {{c->d_lat, sizeof(uint32_t) * (size_t)c->lat_words * c->p_pad},
-            {c->d_E, sizeof(int32_t) * c->p_pad},
-            {c->d_M, sizeof(int32_t) * c->p_pad},
-            {c->d_cnt, sizeof(uint64_t) * 2 * c->p_pad},
-            {c->d_lnw, sizeof(double) * nb},
-            {c->d_P, sizeof(double) * nb},
-            {c->d_lnw_prod, sizeof(double) * nb},
-            {c->d_thr, sizeof(uint32_t) * nb * c->n_de},
-            {c->d_H, sizeof(uint64_t) * nb},
-            {c->d_samples, sizeof(uint64_t) * 3 * nb}};
+    return {{c->d_lat, 4, (size_t)c->lat_words, 0},
+            {c->d_E, 4, 1, 0},
+            {c->d_M, 4, 1, 0},
+            {c->d_cnt, 8, 2, 0},
+            {c->d_lnw, 8, 1, nb},
+            {c->d_P, 8, 1, nb},
+            {c->d_lnw_prod, 8, 1, nb},
+            {c->d_thr, 4, 1, nb * c->n_de},
+            {c->d_H, 8, 1, nb},
+            {c->d_samples, 8, 1, 3 * nb}};
+}
+
+constexpr int32_t kCkptVersion = 3;
+
+// Spins of a checkpoint's lattice (rows x p words) are values of the model: Potts
+// bytes below q, and the bits / bytes past site L - 1 of a row's last word zero.
+bool lattice_valid(const muca_ctx *c, const uint32_t *lat)
+{
+    const int per = c->model == MUCA_ISING ? 32 : 4;
+    const int last = c->L - per * (c->row_words - 1);  // sites in a row's last word
+    for (int k = 0; k < c->lat_words; ++k) {
+        const bool lastw = (k % c->row_words) == c->row_words - 1;
+        const uint32_t *row = lat + (size_t)k * c->p;
+        for (int i = 0; i < c->p; ++i) {
+            const uint32_t w = row[i];
+            if (c->model == MUCA_ISING) {
+                if (lastw && last < 32 && (w >> last) != 0u) return false;
+            } else {
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t v = (w >> (8 * b)) & 0xFFu;
+                    if ((lastw && b >= last) ? v != 0u : v >= (uint32_t)c->q) return false;
+                }
+            }
+        }
+    }
+    return true;
 }
 }  // namespace
 
@@ -670,7 +701,7 @@ int muca_save(muca_ctx *ctx, const char *path)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "MUCACKP1", 8);
-    h.version = 2;
+    h.version = kCkptVersion;
     h.model = ctx->model;
     h.L = ctx->L;
     h.q = ctx->q;
@@ -691,12 +722,20 @@ int muca_save(muca_ctx *ctx, const char *path)
     std::vector<uint8_t> buf;
     for (const Blob &b : blobs(ctx)) {
         if (!ok) break;
-        buf.resize(b.bytes);
-        if (cudaMemcpy(buf.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        const size_t dev_bytes = b.elem * (b.n ? b.n : b.rows * (size_t)ctx->p_pad);
+        buf.resize(dev_bytes);
+        if (cudaMemcpy(buf.data(), b.dev, dev_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
             std::fclose(f);
             return cuda_fail(cudaGetLastError(), "checkpoint read-back");
         }
-        ok = std::fwrite(buf.data(), 1, b.bytes, f) == b.bytes;
+        if (b.n) {
+            ok = std::fwrite(buf.data(), 1, dev_bytes, f) == dev_bytes;
+        } else {
+            // the p chains of every row, without the padding columns
+            const size_t row = b.elem * (size_t)ctx->p;
+            for (size_t r = 0; r < b.rows && ok; ++r)
+                ok = std::fwrite(buf.data() + r * b.elem * (size_t)ctx->p_pad, 1, row, f) == row;
+        }
     }
     ok = (std::fclose(f) == 0) && ok;
     return ok ? MUCA_OK : fail(MUCA_ERR_IO, std::string("write failed: ") + path);
@@ -710,9 +749,14 @@ int muca_load(muca_ctx **out, const char *path, void *cuda_stream)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(MUCA_ERR_IO, std::string("cannot open ") + path);
     CkptHeader h;
-    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "MUCACKP1", 8) != 0 || h.version != 2) {
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "MUCACKP1", 8) != 0) {
         std::fclose(f);
         return fail(MUCA_ERR_IO, "not a checkpoint file (bad header)");
+    }
+    if (h.version != kCkptVersion) {
+        std::fclose(f);
+        return fail(MUCA_ERR_IO, "checkpoint format version " + std::to_string(h.version) + " (this library reads " +
+                                     std::to_string(kCkptVersion) + ")");
     }
     muca_ctx *ctx = nullptr;
     int rc = muca_init(&ctx, h.model, h.L, h.q, h.p, h.seed, &h.cfg, cuda_stream);
@@ -720,21 +764,66 @@ int muca_load(muca_ctx **out, const char *path, void *cuda_stream)
         std::fclose(f);
         return rc;
     }
-    std::vector<uint8_t> buf;
+    auto bail = [&](int code, const std::string &msg) {
+        std::fclose(f);
+        muca_destroy(ctx);
+        return code == MUCA_ERR_CUDA ? cuda_fail(cudaGetLastError(), msg.c_str()) : fail(code, msg);
+    };
+    std::vector<uint8_t> buf, dev;
+    std::vector<uint8_t> chain_state[4];  // lattice, E, M, counts as read (rows x p)
+    int bi = 0;
     for (const Blob &b : blobs(ctx)) {
-        buf.resize(b.bytes);
-        if (std::fread(buf.data(), 1, b.bytes, f) != b.bytes) {
-            std::fclose(f);
-            muca_destroy(ctx);
-            return fail(MUCA_ERR_IO, "checkpoint truncated");
+        const size_t fb = b.file_bytes(ctx);
+        buf.resize(fb);
+        if (std::fread(buf.data(), 1, fb, f) != fb) return bail(MUCA_ERR_IO, "checkpoint truncated");
+        if (b.n) {
+            if (cudaMemcpy(b.dev, buf.data(), fb, cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(MUCA_ERR_CUDA, "checkpoint upload");
+        } else {
+            if (bi == 0 && !lattice_valid(ctx, reinterpret_cast<const uint32_t *>(buf.data())))
+                return bail(MUCA_ERR_IO, "checkpoint holds spins outside the model");
+            // scatter the p chains of every row into the padded layout (padding zero)
+            const size_t row = b.elem * (size_t)ctx->p, drow = b.elem * (size_t)ctx->p_pad;
+            dev.assign(drow * b.rows, 0);
+            for (size_t r = 0; r < b.rows; ++r) std::memcpy(dev.data() + r * drow, buf.data() + r * row, row);
+            if (cudaMemcpy(b.dev, dev.data(), dev.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(MUCA_ERR_CUDA, "checkpoint upload");
+            chain_state[bi] = buf;
         }
-        if (cudaMemcpy(b.dev, buf.data(), b.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-            std::fclose(f);
-            muca_destroy(ctx);
-            return cuda_fail(cudaGetLastError(), "checkpoint upload");
-        }
+        ++bi;
     }
     std::fclose(f);
+    // E, M and the state counts must be those of the spins: recount them on the device
+    // and compare (a chain whose E does not match its spins would walk its bin off the
+    // weight table).  The uploads ran on the legacy stream, the recount runs on the
+    // context's stream: wait for both.
+    if (cudaDeviceSynchronize() != cudaSuccess || (rc = launch_recount(ctx)) ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        if (!rc) rc = cuda_fail(cudaGetLastError(), "checkpoint check");
+        muca_destroy(ctx);
+        return rc;
+    }
+    const int32_t *E_f = reinterpret_cast<const int32_t *>(chain_state[1].data());
+    const int32_t *M_f = reinterpret_cast<const int32_t *>(chain_state[2].data());
+    const uint64_t *C_f = reinterpret_cast<const uint64_t *>(chain_state[3].data());
+    std::vector<int32_t> E(ctx->p), M(ctx->p);
+    std::vector<uint64_t> C(2 * (size_t)ctx->p);
+    bool same = cudaMemcpy(E.data(), ctx->d_E, 4 * (size_t)ctx->p, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                cudaMemcpy(M.data(), ctx->d_M, 4 * (size_t)ctx->p, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                cudaMemcpy(C.data(), ctx->d_cnt, 8 * (size_t)ctx->p, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                cudaMemcpy(C.data() + ctx->p, ctx->d_cnt + ctx->p_pad, 8 * (size_t)ctx->p, cudaMemcpyDeviceToHost) ==
+                    cudaSuccess;
+    if (!same) {
+        rc = cuda_fail(cudaGetLastError(), "checkpoint check");
+        muca_destroy(ctx);
+        return rc;
+    }
+    same = std::memcmp(E.data(), E_f, 4 * (size_t)ctx->p) == 0 && std::memcmp(M.data(), M_f, 4 * (size_t)ctx->p) == 0 &&
+           (ctx->model != MUCA_POTTS || std::memcmp(C.data(), C_f, 16 * (size_t)ctx->p) == 0);
+    if (!same) {
+        muca_destroy(ctx);
+        return fail(MUCA_ERR_IO, "checkpoint energies do not match its spins");
+    }
     ctx->ktab_dirty = 1;
     ctx->iteration = h.iteration;
     ctx->sweeps_therm = h.sweeps_therm;

@@ -884,6 +884,229 @@ __device__ __forceinline__ void potts_count_word(uint32_t word, uint32_t (&cnt)[
     for (int k = 0; k < 8; ++k) cnt[k] += zero_bytes_ws(word ^ (0x01010101u * (uint32_t)k));
 }
 
+// Potts decider for rows of whole ring slots (RW a multiple of 8: L % 32 == 0).  The 32
+// sites of a slot are one unrolled block, so every word index in it is a constant:
+// the next word's records and upper neighbour are read while the current word is
+// decided (the next slot's first word while a slot's last word is), and what is left
+// per word is the upper neighbour's column correction, byte-parallel.  Per site, as in
+// the per-word form: two byte extractions, two bin changes, three selects, the two
+// table loads and the compare.  With the bookkeeper (BOOKW) the decider hands over,
+// per word, the corrected column words, the accepted-byte mask and the old spins (and
+// the proposals, for records), one snapshot block per slot, from which the bookkeeper
+// rebuilds every attempt's bin; without it the decider counts the shared histogram
+// itself (HIST).  Returns the state after the last attempt in P0 / P1 / ap.
+constexpr int kPSnapSlots = 2;  // snapshot blocks of the slot form (one ring slot each)
+
+// byte-wise "not zero" of words whose bytes are below 8 (no masking needed)
+__device__ __forceinline__ uint32_t nz_bytes8(uint32_t x) { return ((x + 0x7F7F7F7Fu) >> 7) & 0x01010101u; }
+
+template <bool BOOKW, bool HIST, bool RECORD, bool TSMEM, bool LSMEM>
+__device__ __forceinline__ void potts_decide_slots(const SweepArgs &a, const uint4 *s_ring, uint4 *s_snap,
+                                                   uint32_t *s_snsn, uint32_t *s_hist, uint32_t *s_hdummy,
+                                                   const uint32_t tab_s, uint32_t *lp, const size_t ls,
+                                                   const int lane, const bool active, uint32_t &P0, uint32_t &P1,
+                                                   bool &ap)
+{
+    static_assert(!RECORD || BOOKW, "records come from the bookkeeper");
+    static_assert(!(HIST && BOOKW), "one histogram owner");
+#define LAT(k) lp[(size_t)(k) * ls]
+    constexpr int NU = 64, RD = kPottsRing;
+    const int L = a.L, RW = a.row_words, spr = RW >> 3;
+    const int total = a.n_sweeps * L * spr;  // slots per launch
+    const char *const tab_g = reinterpret_cast<const char *>(a.ktab) - tab_s;
+    auto tload = [&](uint32_t o) -> uint32_t {
+        return TSMEM ? lds_u32(o) : ldg_nc_u32(reinterpret_cast<const uint32_t *>(tab_g + o));
+    };
+    // bin of a table row address: (P - tab_s) / 36 = ((P - tab_s) / 4) * 9^-1 mod 2^32
+    auto bin_of = [&](uint32_t P) { return (int)(((P - tab_s) >> 2) * 0x38E38E39u); };
+    struct Word {
+        uint4 u;                 // acceptance draws
+        uint32_t R, SN, C0, C1;  // old spins, proposals, column words (previous attempt rejected / accepted)
+    };
+    // a word's columns: the producer's counts plus the upper neighbour U (row above,
+    // final): + [U == s] - [U == s'] = nz(U ^ s') - nz(U ^ s) per byte
+    auto columns = [](Word &x, const uint4 &r1, uint32_t U) {
+        x.R = r1.w;
+        x.SN = r1.x;
+        const uint32_t d = nz_bytes8(U ^ r1.x) - nz_bytes8(U ^ r1.w);
+        x.C0 = r1.y + d;  // every byte of the result is a count in 0..8: the borrows cancel
+        x.C1 = r1.z + d;
+    };
+    auto up_row = [&](int y) { return (y == 0 ? L - 1 : y - 1) * RW; };
+
+    int y = 0, sl = 0;  // row and slot in the row
+    uint32_t first_new = 0u;
+    Word cur;
+    bar_sync(kBarFullU + 0, NU);
+    {
+        cur.u = s_ring[lane];
+        const uint4 r1 = s_ring[32 + lane];
+        columns(cur, r1, LAT(up_row(0)));
+    }
+    uint32_t K0 = byte_of(cur.C0, 0), K1 = byte_of(cur.C1, 0);
+    uint32_t D0 = 36u * K0 - 144u, D1 = 36u * K1 - 144u;
+    uint32_t A0 = tload(P0 + 4u * K0), A1 = tload(P1 + 4u * K1);
+
+    for (int s = 0; s < total; ++s) {
+        const bool has_next = s + 1 < total;
+        int y1 = y, sl1 = sl + 1;
+        if (sl1 == spr) {
+            sl1 = 0;
+            y1 = (y + 1 == L) ? 0 : y + 1;
+        }
+        const bool row_start = sl == 0, row_end = sl == spr - 1;
+        const uint4 *src = s_ring + (s % RD) * 16 * 32 + lane;
+        const int kr = y * RW + sl * 8, ku = up_row(y) + sl * 8;
+        const int b = s % kPSnapSlots;
+        if (BOOKW && s >= kPSnapSlots) bar_sync(kBarEmptyS + b, 64);
+        uint4 *snap = s_snap + b * 8 * 32 + lane;
+        uint32_t Fm = 0u;  // bytes of accepted sites of the current word
+        Word nx = cur;
+        uint4 nr1 = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t nU = 0u;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int w = j >> 2, k = j & 3;
+            if (k == 0) {
+                // records of the next word: in this slot, or the next slot's first
+                if (w < 7) {
+                    nx.u = src[(2 * w + 2) * 32];
+                    nr1 = src[(2 * w + 3) * 32];
+                    nU = LAT(ku + w + 1);
+                } else if (has_next) {
+                    bar_sync(kBarFullU + (s + 1) % RD, NU);
+                    const uint4 *src1 = s_ring + ((s + 1) % RD) * 16 * 32 + lane;
+                    nx.u = src1[0];
+                    nr1 = src1[32];
+                    nU = LAT(up_row(y1) + sl1 * 8);
+                }
+            }
+            if (k == 1 && (w < 7 || has_next)) {
+                columns(nx, nr1, nU);
+                if (w == 7 && sl1 != 0) {
+                    // the next slot starts mid-row: its first site's left neighbour is this
+                    // slot's last site (old spin if that attempt is rejected, else proposal)
+                    const uint32_t lold = cur.R >> 24, lsn = cur.SN >> 24;
+                    const uint32_t s0 = nx.R & 0xFFu, sn0 = nx.SN & 0xFFu;
+                    nx.C0 = nx.C0 + (lold == s0 ? 1u : 0u) - (lold == sn0 ? 1u : 0u);
+                    nx.C1 = nx.C1 + (lsn == s0 ? 1u : 0u) - (lsn == sn0 ? 1u : 0u);
+                }
+            }
+            if (w == 7 && k == 1 && row_end) {
+                // the row's last site: its right neighbour is site 0 of the row, updated
+                const uint32_t s3 = cur.R >> 24, sn3 = cur.SN >> 24;
+                const uint32_t dK = ((first_new == s3 ? 1u : 0u) - (first_new == sn3 ? 1u : 0u)) << 24;
+                cur.C0 += dK;
+                cur.C1 += dK;
+            }
+            // 1. candidates of the next site (offsets resolved by the previous decision)
+            const uint32_t Kn0 = k < 3 ? byte_of(cur.C0, k + 1) : byte_of(nx.C0, 0);
+            const uint32_t Kn1 = k < 3 ? byte_of(cur.C1, k + 1) : byte_of(nx.C1, 0);
+            const uint32_t Dn0 = 36u * Kn0 - 144u, Dn1 = 36u * Kn1 - 144u;
+            const uint32_t Pb = ap ? P1 : P0;
+            const uint32_t PbD = Pb + (ap ? D1 : D0);
+            uint32_t A0n = 0u, A1n = 0u;
+            if (j < 31 || has_next) {
+                A0n = tload(Pb + 4u * Kn0);
+                A1n = tload(PbD + 4u * Kn1);
+            }
+            // 2. decision of this site
+            const uint32_t u = k == 0 ? cur.u.x : k == 1 ? cur.u.y : k == 2 ? cur.u.z : cur.u.w;
+            const bool acc = u < (ap ? A1 : A0);
+            Fm |= acc ? (0xFFu << (8 * k)) : 0u;
+            if (j == 0 && row_start) first_new = acc ? (cur.SN & 0xFFu) : (cur.R & 0xFFu);
+            if (HIST) red_shared(active ? s_hist + bin_of(acc ? PbD : Pb) : s_hdummy, 1u);
+            // 3. state of the next site
+            P0 = Pb;
+            P1 = PbD;
+            D0 = Dn0;
+            D1 = Dn1;
+            A0 = A0n;
+            A1 = A1n;
+            ap = acc;
+            if (k == 3) {
+                LAT(kr + w) = (cur.R & ~Fm) | (cur.SN & Fm);
+                if (BOOKW) {
+                    snap[w * 32] = make_uint4(cur.C0, cur.C1, Fm, cur.R);
+                    if (RECORD) s_snsn[(b * 8 + w) * 32 + lane] = cur.SN;
+                }
+                Fm = 0u;
+                cur = nx;
+            }
+        }
+        // the slot's records are all read: release it
+        if (s < total - RD) bar_arrive(kBarEmptyU + s % RD, NU);
+        if (BOOKW) bar_arrive(kBarFullS + b, 64);
+        y = y1;
+        sl = sl1;
+    }
+#undef LAT
+}
+
+// Bookkeeper of the slot form: every attempt's bin from the snapshot block of a slot
+// (column words, accepted bytes, old spins, proposals), the histogram (single
+// attempts, or pairs of attempts: HPAIR), the state counts and the records.
+template <bool HIST, bool HPAIR, bool RECORD>
+__device__ __forceinline__ void potts_book_slots(const SweepArgs &a, const uint4 *s_snap, const uint32_t *s_snsn,
+                                                 uint32_t *s_hist, uint32_t *s_hdummy, const int lane,
+                                                 const bool active, const int c, int bin, uint64_t &bk_lo,
+                                                 uint64_t &bk_hi)
+{
+    const int L = a.L, RW = a.row_words, V = L * L, spr = RW >> 3;
+    const int total = a.n_sweeps * L * spr;
+    const int per_sweep = L * spr;
+    bool ap = false;  // previous attempt accepted
+    for (int s = 0; s < total; ++s) {
+        const int b = s % kPSnapSlots;
+        bar_sync(kBarFullS + b, 64);
+        const uint4 *snap = s_snap + b * 8 * 32 + lane;
+#pragma unroll 2
+        for (int w = 0; w < 8; ++w) {
+            const uint4 sn = snap[w * 32];  // (C0, C1, Fm, R)
+            int bk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool acc = (sn.z >> (8 * k)) & 1u;
+                const int col = (int)(ap ? byte_of(sn.y, k) : byte_of(sn.x, k));
+                bin += acc ? col - 4 : 0;
+                bk[k] = bin;
+                ap = acc;
+                if (HIST && !HPAIR) red_shared(active ? s_hist + bin : s_hdummy, 1u);
+            }
+            if (HPAIR) {
+                // one count per pair of attempts: (0, 1) and (2, 3)
+                red_shared(active ? s_hist + 9 * bk[0] + 4 + (bk[1] - bk[0]) : s_hdummy, 1u);
+                red_shared(active ? s_hist + 9 * bk[2] + 4 + (bk[3] - bk[2]) : s_hdummy, 1u);
+            }
+            if (RECORD) {
+                // accepted sites move one count from the old state to the new one; a
+                // rejected site moves one from state 0 to state 0 (no branch)
+                const uint32_t SN = s_snsn[(b * 8 + w) * 32 + lane];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const bool acc = (sn.z >> (8 * k)) & 1u;
+                    potts_count_move(bk_lo, bk_hi, acc ? byte_of(sn.w, k) : 0u, acc ? byte_of(SN, k) : 0u);
+                }
+            }
+        }
+        if (s < total - kPSnapSlots) bar_arrive(kBarEmptyS + b, 64);
+        if (RECORD && (s + 1) % per_sweep == 0 && active) {
+            const int sw = s / per_sweep;
+            const int E = bin - 2 * V;
+            const int M = 8 * potts_count_max(bk_lo, bk_hi) - V;
+            if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
+            if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
+            if (a.samples) {
+                const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
+                unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
+                atomicAdd(&sp[bin], 1ull);
+                atomicAdd(&sp[a.n_bins + bin], am);
+                atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+            }
+        }
+    }
+}
+
 // PBOOK: a fifth warp, the bookkeeper, takes the histogram, the state counts and the
 // records from per-word snapshots (iteration and production launches of the
 // standalone kernel); the decider then runs on warp 1, alone on its SM sub-partition,
@@ -906,7 +1129,12 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     // the histogram is followed by one slot per lane (kHistDummy) for inactive lanes
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) + kHistDummy : 0);
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [ring][8 words][2][32]
-    uint4 *s_psnap = s_ring + kPottsRing * 16 * 32;                                      // [kRingS][2][32]
+    uint4 *s_psnap = s_ring + kPottsRing * 16 * 32;  // [kRingS][2][32]; slot form: [kPSnapSlots][8][32]
+    uint32_t *s_snsn = reinterpret_cast<uint32_t *>(s_psnap + kPSnapSlots * 8 * 32);  // [kPSnapSlots][8][32]
+    // slot form of the decider (and bookkeeper): rows of whole slots, with the
+    // histogram in shared memory or kept by the bookkeeper, records by the bookkeeper
+    constexpr bool SLOTS_OK = (BOOKW || !RECORD) && (!HIST || BOOKW || HSMEM);
+    const bool slots = SLOTS_OK && (a.row_words % kPottsSlotWords) == 0;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vw = BOOKW ? (warp == 0 ? 1 : warp == 1 ? 0 : warp) : warp;  // role: 0 decider, 1..3 producers, 4 bookkeeper
@@ -1051,6 +1279,11 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             x.C1 = c1 << 2;
         };
 
+        if (slots) {
+            potts_decide_slots<BOOKW, HIST && !BOOKW && SLOTS_OK, RECORD && BOOKW, TSMEM, LSMEM>(
+                a, s_ring, s_psnap, s_snsn, s_hist, s_hdummy, tab_s, LSMEM ? s_lat + lane : glat,
+                LSMEM ? (size_t)32 : gstride, lane, active, P0, P1, ap);
+        } else {
         const int total_words = a.n_sweeps * L * RW;
         // the first word
         bar_sync(kBarFullU + 0, NU);
@@ -1195,6 +1428,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
             w = w1;
             it = it1;
         }
+        }
         if (active) {
             if (HIST && !BOOKW && !HSMEM && run)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[run_bin]), (unsigned long long)run);
@@ -1217,6 +1451,14 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
 #undef TABLOAD
         if (LSMEM)
             for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
+    } else if (BOOKW && vw == 4 && slots) {
+        potts_book_slots<HIST, HPAIR, RECORD>(a, s_psnap, s_snsn, s_hist, s_hdummy, lane, active, c, bk_bin0, bk_lo,
+                                             bk_hi);
+        if (active && RECORD) {
+            a.M[c] = 8 * potts_count_max(bk_lo, bk_hi) - V;
+            a.cnt[c] = bk_lo;
+            a.cnt[a.p_pad + c] = bk_hi;
+        }
     } else if (BOOKW && vw == 4) {
         // ---------------- bookkeeper: histogram, state counts, records -----------
         // table addresses: shared-memory addresses, or byte offsets into the global table
@@ -1318,7 +1560,13 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
 // the bookkeeper, its snapshot ring
 __host__ __device__ constexpr size_t potts_ws_extra_smem(bool book = false)
 {
-    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) + (book ? (size_t)kRingS * 2 * 32 * sizeof(uint4) : 0);
+    // snapshots: the larger of the word form ([kRingS][2][32] uint4) and the slot form
+    // ([kPSnapSlots][8][32] uint4 + [kPSnapSlots][8][32] proposals)
+    return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) +
+           (!book ? 0
+            : (size_t)kRingS * 2 * 32 * sizeof(uint4) > (size_t)kPSnapSlots * 8 * 32 * (sizeof(uint4) + sizeof(uint32_t))
+                ? (size_t)kRingS * 2 * 32 * sizeof(uint4)
+                : (size_t)kPSnapSlots * 8 * 32 * (sizeof(uint4) + sizeof(uint32_t)));
 }
 }  // namespace ws
 }  // namespace muca

@@ -64,6 +64,55 @@ def test_truncated_checkpoint_is_io_error(muca, tmp_path):
     h.close()
 
 
+def _ckpt_offsets(m, path, model, L, p, n_bins, n_thr):
+    """Byte offsets of the lattice and of E in a checkpoint file (format version 3:
+    the header, then the lattice as row words x p chains, E, M, the two count words
+    per chain, then the per-bin arrays: ln W, P, production ln W, the n_thr
+    thresholds, H and the three production sums)."""
+    lat_words = L * ((L + 31) // 32 if model == m.MUCA_ISING else (L + 3) // 4)
+    body = 4 * lat_words * p + 4 * p + 4 * p + 16 * p + 8 * n_bins * 3 + 4 * n_thr + 8 * n_bins + 24 * n_bins
+    header = os.path.getsize(path) - body
+    assert 0 < header < 512, header
+    return header, header + 4 * lat_words * p
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model,L,q", [(0, 16, 2), (1, 12, 8)])
+def test_inconsistent_checkpoint_is_io_error(muca, tmp_path, model, L, q):
+    """A checkpoint whose spins lie outside the model, or whose energies are not those
+    of its spins, is refused with MUCA_ERR_IO before any sweep can walk a chain off the
+    weight table."""
+    m = muca
+    p = 37
+    path = str(tmp_path / "ok.ckpt")
+    with m.Muca(model, L, q, p, 5) as g:
+        g.iterate(3)
+        g.update_weights()
+        g.save(path)
+        n_bins, n_thr = g.n_bins, g.get_thresholds().size
+    lat0, e0 = _ckpt_offsets(m, path, model, L, p, n_bins, n_thr)
+    data = bytearray(open(path, "rb").read())
+    cases = {}
+    bad = bytearray(data)
+    bad[e0 + 4 * 3] ^= 0x04            # chain 3's E off by a multiple of the level spacing
+    cases["energy"] = bad
+    bad = bytearray(data)
+    if model == m.MUCA_POTTS:
+        bad[lat0 + 4 * 5] = 9           # a Potts spin of chain 5 outside 0..q-1
+    else:
+        # a bit past site L - 1 in the last word of row 0 of chain 5 (L = 16 < 32)
+        bad[lat0 + 4 * 5 + 3] |= 0x80
+    cases["spin"] = bad
+    for name, blob in cases.items():
+        bpath = str(tmp_path / (name + ".ckpt"))
+        open(bpath, "wb").write(bytes(blob))
+        with pytest.raises(m.MucaError) as ei:
+            m.Muca.load(bpath)
+        assert ei.value.code == m._muca.MUCA_ERR_IO, name
+    h = m.Muca.load(path)
+    h.close()
+
+
 _OOM_CHILD = r"""
 import ctypes, sys
 sys.path.insert(0, %r)
