@@ -108,6 +108,7 @@ struct SweepPlan {
     bool t16;               // compact with a table of 16-bit threshold halves: three blocks per SM
     int chains_per_block;
     size_t smem_bytes;      // staging of the plan (table, histogram, lattices)
+    size_t table_bytes, hist_bytes, lat_bytes;  // its parts (0: not staged)
 };
 
 // Device view of one lattice of a batch (pointers into its context).
@@ -258,7 +259,9 @@ constexpr size_t kNoallocScratchBytes = rw_bin_part_bytes(kNoallocMaxBins) + rw_
 cudaError_t launch_reweight_buffers(double *scratch, const uint64_t *samples, const double *lnw, int model, int L,
                                     int q, const double *d_betas, int n_beta, int precision, double *d_out, int n_sm,
                                     cudaStream_t st);
-size_t ws_extra_smem(int model, bool compact = false);
+// shared memory of a warp-specialised launch beyond its staging, for launches with a
+// histogram and / or records (the defaults: the largest)
+size_t ws_extra_smem(int model, bool compact = false, bool hist = true, bool record = true);
 // multimagnetic Ising ensemble (muma.cu)
 int launch_muma_thresholds(muca_ctx *ctx);
 int launch_muma_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,

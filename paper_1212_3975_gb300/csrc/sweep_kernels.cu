@@ -477,6 +477,9 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
     pl.hist_pairs = allow_pairs && ws && pl.table_smem && pl.hist_smem && pl.lattice_smem && used - hist + pairs <= cap;
     if (pl.hist_pairs) used += pairs - hist;
     pl.smem_bytes = used;
+    pl.table_bytes = pl.table_smem ? table : 0;
+    pl.hist_bytes = pl.hist_smem ? (pl.hist_pairs ? pairs : hist) : 0;
+    pl.lat_bytes = pl.lattice_smem ? lat : 0;
     // More groups of 32 chains than SMs (the throughput regime): a plan whose block
     // takes more than half of an SM's shared memory runs one block per SM and leaves
     // the other groups waiting for a second wave.  The compact Ising staging keeps the
@@ -493,6 +496,8 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
             pl.lattice_smem = false;
             pl.hist_pairs = false;
             pl.smem_bytes = table + hist;
+            pl.hist_bytes = hist;
+            pl.lat_bytes = 0;
         }
         // More groups than two per SM, and rows of whole words (at least two: the
         // stream decider): the table of the upper 16-bit halves of the thresholds (ties
@@ -512,6 +517,9 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
             pl.lattice_smem = false;
             pl.hist_pairs = false;
             pl.smem_bytes = table16 + hist;
+            pl.table_bytes = table16;
+            pl.hist_bytes = hist;
+            pl.lat_bytes = 0;
         }
     }
     return pl;

@@ -70,17 +70,22 @@ cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size
 }  // namespace
 
 // shared memory of the warp-specialised kernels beyond the staging of the plan
-size_t ws_extra_smem(int model, bool compact)
+size_t ws_extra_smem(int model, bool compact, bool hist, bool record)
 {
     const int ring = compact ? kCompactRing : kRingU;
-    return model == MUCA_ISING ? (size_t)ring * 8 * 32 * sizeof(uint4) + (size_t)kRingS * 32 * sizeof(Snap)
-                               : potts_ws_extra_smem(true);
+    return model == MUCA_ISING
+               ? (size_t)ring * 8 * 32 * sizeof(uint4) + ((hist || record) ? (size_t)kRingS * 32 * sizeof(Snap) : 0)
+               : potts_ws_extra_smem(hist, record);
 }
 
 cudaError_t launch_ws_sweep(const SweepArgs &a, const SweepPlan &pl, int model, int blocks, bool hist, bool record,
                             cudaStream_t st)
 {
-    const size_t smem = pl.smem_bytes + ws_extra_smem(model, pl.compact);
+    // what this launch uses: no histogram (and no snapshots) in thermalisation, no
+    // histogram in production; the rest of the SM's shared memory stays L1 cache,
+    // which holds the hot rows of a table in global memory
+    const size_t smem = pl.table_bytes + (hist ? pl.hist_bytes : 0) + pl.lat_bytes +
+                        ws_extra_smem(model, pl.compact, hist, record);
     if (model == MUCA_ISING) {
         if (hist && record) return ws_staging<MUCA_ISING, true, true>(a, pl, blocks, smem, st);
         if (hist) return ws_staging<MUCA_ISING, true, false>(a, pl, blocks, smem, st);

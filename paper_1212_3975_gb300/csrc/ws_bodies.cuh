@@ -893,14 +893,16 @@ __device__ __forceinline__ void potts_count_word(uint32_t word, uint32_t (&cnt)[
 // table loads and the compare.  With the bookkeeper (BOOKW) the decider hands over,
 // per word, the corrected column words, the accepted-byte mask and the old spins (and
 // the proposals, for records), one snapshot block per slot, from which the bookkeeper
-// rebuilds every attempt's bin; without it the decider counts the shared histogram
-// itself (HIST).  Returns the state after the last attempt in P0 / P1 / ap.
+// rebuilds every attempt's bin for its histogram (BHIST; without a histogram it gets
+// the bin at each word's end instead); without the bookkeeper the decider counts the
+// shared histogram itself (HIST).  Returns the state after the last attempt in P0 /
+// P1 / ap.
 constexpr int kPSnapSlots = 2;  // snapshot blocks of the slot form (one ring slot each)
 
 // byte-wise "not zero" of words whose bytes are below 8 (no masking needed)
 __device__ __forceinline__ uint32_t nz_bytes8(uint32_t x) { return ((x + 0x7F7F7F7Fu) >> 7) & 0x01010101u; }
 
-template <bool BOOKW, bool HIST, bool RECORD, bool TSMEM, bool LSMEM>
+template <bool BOOKW, bool HIST, bool RECORD, bool TSMEM, bool LSMEM, bool BHIST>
 __device__ __forceinline__ void potts_decide_slots(const SweepArgs &a, const uint4 *s_ring, uint4 *s_snap,
                                                    uint32_t *s_snsn, uint32_t *s_hist, uint32_t *s_hdummy,
                                                    const uint32_t tab_s, uint32_t *lp, const size_t ls,
@@ -1027,7 +1029,9 @@ __device__ __forceinline__ void potts_decide_slots(const SweepArgs &a, const uin
             if (k == 3) {
                 LAT(kr + w) = (cur.R & ~Fm) | (cur.SN & Fm);
                 if (BOOKW) {
-                    snap[w * 32] = make_uint4(cur.C0, cur.C1, Fm, cur.R);
+                    // the bookkeeper rebuilds every attempt's bin from the column words
+                    // for its histogram (BHIST), else it needs the bin at the word's end
+                    snap[w * 32] = make_uint4(BHIST ? cur.C0 : (ap ? P1 : P0), cur.C1, Fm, cur.R);
                     if (RECORD) s_snsn[(b * 8 + w) * 32 + lane] = cur.SN;
                 }
                 Fm = 0u;
@@ -1044,64 +1048,79 @@ __device__ __forceinline__ void potts_decide_slots(const SweepArgs &a, const uin
 }
 
 // Bookkeeper of the slot form: every attempt's bin from the snapshot block of a slot
-// (column words, accepted bytes, old spins, proposals), the histogram (single
-// attempts, or pairs of attempts: HPAIR), the state counts and the records.
+// (column words, accepted bytes, old spins, proposals) for the histogram (single
+// attempts, or pairs of attempts: HPAIR), and for records the state counts and the
+// (E, M) records.  The state counts live in shared memory, one 32-bit counter per
+// (state, lane) and a ninth row for rejected attempts, updated with red.shared (no
+// result, so consecutive updates do not wait on one another): an accepted site moves
+// one count from its old state to its new one.
 template <bool HIST, bool HPAIR, bool RECORD>
 __device__ __forceinline__ void potts_book_slots(const SweepArgs &a, const uint4 *s_snap, const uint32_t *s_snsn,
-                                                 uint32_t *s_hist, uint32_t *s_hdummy, const int lane,
-                                                 const bool active, const int c, int bin, uint64_t &bk_lo,
-                                                 uint64_t &bk_hi)
+                                                 uint32_t *s_hist, uint32_t *s_hdummy, uint32_t *s_cnt,
+                                                 const uint32_t tab_s, const int lane, const bool active, const int c,
+                                                 int bin)
 {
     const int L = a.L, RW = a.row_words, V = L * L, spr = RW >> 3;
     const int total = a.n_sweeps * L * spr;
     const int per_sweep = L * spr;
-    bool ap = false;  // previous attempt accepted
+    uint32_t *const cl = s_cnt + lane;  // [9][32]: counters of states 0..7, rejected
+    bool ap = false;                    // previous attempt accepted
+    uint32_t last_row = 0u;             // bin row after the slot (without a histogram)
     for (int s = 0; s < total; ++s) {
         const int b = s % kPSnapSlots;
         bar_sync(kBarFullS + b, 64);
         const uint4 *snap = s_snap + b * 8 * 32 + lane;
 #pragma unroll 2
         for (int w = 0; w < 8; ++w) {
-            const uint4 sn = snap[w * 32];  // (C0, C1, Fm, R)
-            int bk[4];
+            const uint4 sn = snap[w * 32];  // (C0 or bin row, C1, Fm, R)
+            if (HIST) {
+                int bk[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const bool acc = (sn.z >> (8 * k)) & 1u;
-                const int col = (int)(ap ? byte_of(sn.y, k) : byte_of(sn.x, k));
-                bin += acc ? col - 4 : 0;
-                bk[k] = bin;
-                ap = acc;
-                if (HIST && !HPAIR) red_shared(active ? s_hist + bin : s_hdummy, 1u);
-            }
-            if (HPAIR) {
-                // one count per pair of attempts: (0, 1) and (2, 3)
-                red_shared(active ? s_hist + 9 * bk[0] + 4 + (bk[1] - bk[0]) : s_hdummy, 1u);
-                red_shared(active ? s_hist + 9 * bk[2] + 4 + (bk[3] - bk[2]) : s_hdummy, 1u);
+                for (int k = 0; k < 4; ++k) {
+                    const bool acc = (sn.z >> (8 * k)) & 1u;
+                    const int col = (int)(ap ? byte_of(sn.y, k) : byte_of(sn.x, k));
+                    bin += acc ? col - 4 : 0;
+                    bk[k] = bin;
+                    ap = acc;
+                    if (!HPAIR) red_shared(active ? s_hist + bin : s_hdummy, 1u);
+                }
+                if (HPAIR) {
+                    // one count per pair of attempts: (0, 1) and (2, 3)
+                    red_shared(active ? s_hist + 9 * bk[0] + 4 + (bk[1] - bk[0]) : s_hdummy, 1u);
+                    red_shared(active ? s_hist + 9 * bk[2] + 4 + (bk[3] - bk[2]) : s_hdummy, 1u);
+                }
+            } else {
+                last_row = sn.x;
             }
             if (RECORD) {
-                // accepted sites move one count from the old state to the new one; a
-                // rejected site moves one from state 0 to state 0 (no branch)
                 const uint32_t SN = s_snsn[(b * 8 + w) * 32 + lane];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const bool acc = (sn.z >> (8 * k)) & 1u;
-                    potts_count_move(bk_lo, bk_hi, acc ? byte_of(sn.w, k) : 0u, acc ? byte_of(SN, k) : 0u);
+                    red_shared(cl + 32u * (acc ? byte_of(sn.w, k) : 8u), 0xFFFFFFFFu);  // - 1
+                    red_shared(cl + 32u * (acc ? byte_of(SN, k) : 8u), 1u);
                 }
             }
         }
         if (s < total - kPSnapSlots) bar_arrive(kBarEmptyS + b, 64);
-        if (RECORD && (s + 1) % per_sweep == 0 && active) {
-            const int sw = s / per_sweep;
-            const int E = bin - 2 * V;
-            const int M = 8 * potts_count_max(bk_lo, bk_hi) - V;
-            if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
-            if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
-            if (a.samples) {
-                const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
-                unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
-                atomicAdd(&sp[bin], 1ull);
-                atomicAdd(&sp[a.n_bins + bin], am);
-                atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+        if (RECORD && (s + 1) % per_sweep == 0) {
+            if (!HIST) bin = (int)(((last_row - tab_s) >> 2) * 0x38E38E39u);  // row / 36
+            if (active) {
+                const int sw = s / per_sweep;
+                const int E = bin - 2 * V;
+                uint32_t mx = 0u;
+#pragma unroll
+                for (int v = 0; v < 8; ++v) mx = max(mx, cl[32 * v]);
+                const int M = 8 * (int)mx - V;
+                if (a.E_rec) a.E_rec[(size_t)sw * a.rec_stride + c] = E;
+                if (a.M_rec) a.M_rec[(size_t)sw * a.rec_stride + c] = M;
+                if (a.samples) {
+                    const unsigned long long am = (unsigned long long)(M < 0 ? -M : M);
+                    unsigned long long *sp = reinterpret_cast<unsigned long long *>(a.samples);
+                    atomicAdd(&sp[bin], 1ull);
+                    atomicAdd(&sp[a.n_bins + bin], am);
+                    atomicAdd(&sp[2 * a.n_bins + bin], am * am);
+                }
             }
         }
     }
@@ -1133,7 +1152,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
     uint32_t *s_snsn = reinterpret_cast<uint32_t *>(s_psnap + kPSnapSlots * 8 * 32);  // [kPSnapSlots][8][32]
     // slot form of the decider (and bookkeeper): rows of whole slots, with the
     // histogram in shared memory or kept by the bookkeeper, records by the bookkeeper
-    constexpr bool SLOTS_OK = (BOOKW || !RECORD) && (!HIST || BOOKW || HSMEM);
+    constexpr bool SLOTS_OK = (BOOKW || !RECORD) && (!HIST || HSMEM);
     const bool slots = SLOTS_OK && (a.row_words % kPottsSlotWords) == 0;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1280,7 +1299,7 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
         };
 
         if (slots) {
-            potts_decide_slots<BOOKW, HIST && !BOOKW && SLOTS_OK, RECORD && BOOKW, TSMEM, LSMEM>(
+            potts_decide_slots<BOOKW, HIST && !BOOKW && SLOTS_OK, RECORD && BOOKW, TSMEM, LSMEM, BOOKW && HIST>(
                 a, s_ring, s_psnap, s_snsn, s_hist, s_hdummy, tab_s, LSMEM ? s_lat + lane : glat,
                 LSMEM ? (size_t)32 : gstride, lane, active, P0, P1, ap);
         } else {
@@ -1452,12 +1471,31 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
         if (LSMEM)
             for (int k = 0; k < a.lat_words; ++k) a.lat[(size_t)k * a.p_pad + c] = s_lat[k * 32 + lane];
     } else if (BOOKW && vw == 4 && slots) {
-        potts_book_slots<HIST, HPAIR, RECORD>(a, s_psnap, s_snsn, s_hist, s_hdummy, lane, active, c, bk_bin0, bk_lo,
-                                             bk_hi);
+        uint32_t *const s_cnt = s_snsn + kPSnapSlots * 8 * 32;  // [9][32] state counters
+        if (RECORD) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                s_cnt[32 * v + lane] = (uint32_t)(bk_lo >> (16 * v)) & 0xFFFFu;
+                s_cnt[32 * (v + 4) + lane] = (uint32_t)(bk_hi >> (16 * v)) & 0xFFFFu;
+            }
+            s_cnt[32 * 8 + lane] = 0u;
+        }
+        const uint32_t tab_s = TSMEM ? (uint32_t)__cvta_generic_to_shared(s_tab) : 0u;
+        potts_book_slots<HIST, HPAIR, RECORD>(a, s_psnap, s_snsn, s_hist, s_hdummy, s_cnt, tab_s, lane, active, c,
+                                             bk_bin0);
         if (active && RECORD) {
-            a.M[c] = 8 * potts_count_max(bk_lo, bk_hi) - V;
-            a.cnt[c] = bk_lo;
-            a.cnt[a.p_pad + c] = bk_hi;
+            uint64_t lo = 0, hi = 0;
+            uint32_t mx = 0u;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint32_t n0 = s_cnt[32 * v + lane], n1 = s_cnt[32 * (v + 4) + lane];
+                lo |= (uint64_t)n0 << (16 * v);
+                hi |= (uint64_t)n1 << (16 * v);
+                mx = max(mx, max(n0, n1));
+            }
+            a.M[c] = 8 * (int)mx - V;
+            a.cnt[c] = lo;
+            a.cnt[a.p_pad + c] = hi;
         }
     } else if (BOOKW && vw == 4) {
         // ---------------- bookkeeper: histogram, state counts, records -----------
@@ -1557,16 +1595,19 @@ __device__ __forceinline__ void potts_ws_body(const SweepArgs &a, const int cblk
 }
 
 // shared memory of the Potts body beyond the staging: the draw/column ring and, with
-// the bookkeeper, its snapshot ring
-__host__ __device__ constexpr size_t potts_ws_extra_smem(bool book = false)
+// the bookkeeper (histogram or records), its snapshots: the larger of the word form
+// ([kRingS][2][32] uint4) and the slot form ([kPSnapSlots][8][32] uint4, and for
+// records the proposals [kPSnapSlots][8][32] and the state counters [9][32])
+__host__ __device__ constexpr size_t potts_ws_extra_smem(bool hist, bool record)
 {
-    // snapshots: the larger of the word form ([kRingS][2][32] uint4) and the slot form
-    // ([kPSnapSlots][8][32] uint4 + [kPSnapSlots][8][32] proposals)
     return (size_t)kPottsRing * 16 * 32 * sizeof(uint4) +
-           (!book ? 0
-            : (size_t)kRingS * 2 * 32 * sizeof(uint4) > (size_t)kPSnapSlots * 8 * 32 * (sizeof(uint4) + sizeof(uint32_t))
+           (!(hist || record) ? 0
+            : (size_t)kRingS * 2 * 32 * sizeof(uint4) >
+                      (size_t)kPSnapSlots * 8 * 32 * sizeof(uint4) +
+                          (record ? (size_t)kPSnapSlots * 8 * 32 * sizeof(uint32_t) + 9 * 32 * sizeof(uint32_t) : 0)
                 ? (size_t)kRingS * 2 * 32 * sizeof(uint4)
-                : (size_t)kPSnapSlots * 8 * 32 * (sizeof(uint4) + sizeof(uint32_t)));
+                : (size_t)kPSnapSlots * 8 * 32 * sizeof(uint4) +
+                      (record ? (size_t)kPSnapSlots * 8 * 32 * sizeof(uint32_t) + 9 * 32 * sizeof(uint32_t) : 0));
 }
 }  // namespace ws
 }  // namespace muca

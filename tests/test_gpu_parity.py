@@ -88,7 +88,7 @@ SWEEP_CASES = [
     (POTTS, 3, 7, 40, 0, 0), (POTTS, 4, 9, 40, 0, 0), (POTTS, 8, 33, 20, 0, 2),
     (POTTS, 5, 65, 20, 0, 0), (POTTS, 6, 40, 20, 64, 2),
     (POTTS, 32, 40, 3, 0, 0), (POTTS, 30, 33, 3, 32, 2), (POTTS, 32, 130, 2, 128, 1),
-    (POTTS, 64, 35, 2, 0, 0), (POTTS, 128, 20, 1, 0, 0)]
+    (POTTS, 64, 35, 2, 0, 0), (POTTS, 128, 20, 1, 0, 0), (POTTS, 160, 8, 1, 0, 0)]
 
 
 @pytest.mark.parametrize("model,L,p,sweeps,cpb,staging", SWEEP_CASES)
@@ -138,7 +138,7 @@ def test_thermalize_bit_exact_with_injected_table(muca, model, L, p):
 
 
 @pytest.mark.parametrize("model,L,p", [(ISING, 8, 37), (ISING, 64, 33), (POTTS, 6, 40),
-                                       (POTTS, 32, 35), (POTTS, 64, 33)])
+                                       (POTTS, 32, 35), (POTTS, 64, 33), (POTTS, 160, 8)])
 def test_produce_records_and_samples(muca, model, L, p):
     q = 2 if model == ISING else 8
     seed = 77
