@@ -74,7 +74,7 @@ size_t ws_extra_smem(int model, bool compact, bool hist, bool record)
 {
     const int ring = compact ? kCompactRing : kRingU;
     return model == MUCA_ISING
-               ? (size_t)ring * 8 * 32 * sizeof(uint4) + ((hist || record) ? (size_t)kRingS * 32 * sizeof(Snap) : 0)
+               ? (size_t)ring * 8 * 32 * sizeof(uint4) + ((hist || record) ? (size_t)kRingS * kSnapWords * 32 * sizeof(Snap) : 0)
                : potts_ws_extra_smem(hist, record);
 }
 

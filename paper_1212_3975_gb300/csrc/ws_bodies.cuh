@@ -33,6 +33,7 @@ namespace ws {
 
 constexpr int kRingU = 4;   // slots of Philox draws (one row word each)
 constexpr int kRingS = 3;   // slots of bookkeeping snapshots
+constexpr int kSnapWords = 2;  // Ising: row words per snapshot slot (one hand-off per pair)
 constexpr int kCompactRing = 3;  // draw-ring slots of the compact Ising staging
 constexpr int kHistDummy = 32;   // histogram slots of inactive lanes (one per lane)
 constexpr int kBarFullU = 1, kBarEmptyU = kBarFullU + kRingU;      // ids 1..8
@@ -82,8 +83,8 @@ struct Snap {
     uint32_t qw;       // site differs from its old left neighbour
     uint32_t flip;     // sites whose spin flipped (= accepted attempts)
     uint32_t rold;     // spins before the word was swept
-    uint32_t pad[3];
-};
+};  // 20 bytes: a lane stride of 5 words, so a warp's accesses of one field hit 32 banks
+static_assert(sizeof(Snap) == 20, "snapshot layout");
 
 // Neighbour planes of one row word: lo/hi = bit-sliced count of the unequal up, down
 // and right neighbours, qw = site differs from its old left neighbour.
@@ -353,15 +354,17 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
         if (it < total - RU) bar_arrive(kBarEmptyU + slot, NU);
         LAT(y * RW + w) = Rw;
         if (BOOK) {
-            const int ss = it % RS;
-            if (it >= RS) bar_sync(kBarEmptyS + ss, 64);
-            Snap *sn = s_snap + ss * 32 + lane;
+            // snapshots are handed over in pairs of words (a launch has an even number
+            // of words: L is even), one barrier hand-off per pair
+            const int pw = it >> 1, half = it & 1, ss = pw % RS;
+            if (half == 0 && pw >= RS) bar_sync(kBarEmptyS + ss, 64);
+            Snap *sn = s_snap + (ss * kSnapWords + half) * 32 + lane;
             sn->lo = cur.lo;
             sn->hi = cur.hi;
             sn->qw = cur.qw;
             sn->flip = cur.R ^ Rw;
             sn->rold = cur.R;
-            bar_arrive(kBarFullS + ss, 64);
+            if (half == 1) bar_arrive(kBarFullS + ss, 64);
         }
         if (lastw) first_new = 0u;
         cur = nx;
@@ -406,7 +409,7 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     uint32_t *s_lat = s_hist + ((HIST && HSMEM) ? ((n_hist + 3) & ~3) + kHistDummy : 0);
     static_assert(RU >= 2 && RU <= kRingU, "draw ring slots");
     uint4 *s_ring = reinterpret_cast<uint4 *>(s_lat + (LSMEM ? a.lat_words * 32 : 0));  // [RU][8][32]
-    Snap *s_snap = reinterpret_cast<Snap *>(s_ring + RU * 8 * 32);                       // [kRingS][32]
+    Snap *s_snap = reinterpret_cast<Snap *>(s_ring + RU * 8 * 32);  // [kRingS][kSnapWords][32]
 
     const int tid = threadIdx.x, lane = tid & 31;
     // chain of this lane: group cblk holds chains cblk * cpg ..; lanes beyond cpg take
@@ -684,15 +687,15 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                             lo = ua ^ ub ^ tr2;
                             hi = (ua & ub) | (tr2 & (ua ^ ub));
                         }
-                        const int ss = it % kRingS;
-                        if (it >= kRingS) bar_sync(kBarEmptyS + ss, 64);
-                        Snap *sn = s_snap + ss * 32 + lane;
+                        const int pw = it >> 1, half = it & 1, ss = pw % kRingS;  // pairs of words
+                        if (half == 0 && pw >= kRingS) bar_sync(kBarEmptyS + ss, 64);
+                        Snap *sn = s_snap + (ss * kSnapWords + half) * 32 + lane;
                         sn->lo = lo;
                         sn->hi = hi;
                         sn->qw = qw;
                         sn->flip = R ^ Rw;
                         sn->rold = R;
-                        bar_arrive(kBarFullS + ss, 64);
+                        if (half == 1) bar_arrive(kBarFullS + ss, 64);
                     }
                     lbit = R >> 31;
                     R = Rn;
@@ -726,10 +729,10 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                 uint32_t pflip = 0u;  // flip of the previous site in this row
                 for (int w = 0; w < RW; ++w, ++it) {
                     const int nb = (w == RW - 1) ? last_bits : 32;
-                    const int ss = it % kRingS;
-                    bar_sync(kBarFullS + ss, 64);
-                    const Snap sn = s_snap[ss * 32 + lane];
-                    if (it < total - kRingS) bar_arrive(kBarEmptyS + ss, 64);
+                    const int pw = it >> 1, half = it & 1, ss = pw % kRingS;  // pairs of words
+                    if (half == 0) bar_sync(kBarFullS + ss, 64);
+                    const Snap sn = s_snap[(ss * kSnapWords + half) * 32 + lane];
+                    if (half == 1 && pw < (total >> 1) - kRingS) bar_arrive(kBarEmptyS + ss, 64);
                     // left neighbour as seen by each site: old left, flipped if the
                     // previous site flipped (not across the row start)
                     const uint32_t lf = (sn.flip << 1) | pflip;
