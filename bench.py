@@ -52,20 +52,22 @@ REASON_BITS = {
 SWEEP_SOURCES = ["paper_1212_3975_gb300/csrc/ws_bodies.cuh", "paper_1212_3975_gb300/csrc/sweep_ws.cu",
                  "paper_1212_3975_gb300/csrc/sweep_kernels.cu"]
 COUNTERS = {
-    # Ising 64x64, one block per SM (p = 1024): profiles/ising_ws_sweep_L64_p1024.md
-    "ising_L64": {"source": "7239a44f398aea87", "inst_per_attempt": 1.869,
-                  "shared_wavefronts_per_attempt": 0.354, "traffic_bytes_per_launch": 681472},
+    # Ising 64x64, p = 1024: 147 blocks of 7 chains, one per SM (the idle lanes of each
+    # warp issue too, so these counts are per attempt of a real chain):
+    # profiles/ising_ws_sweep_L64_p1024.md
+    "ising_L64": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 8.508,
+                  "shared_wavefronts_per_attempt": 1.013, "traffic_bytes_per_launch": 2564864},
     # Ising 64x64, compact staging, two blocks per SM (p = 9728):
     # profiles/ising_ws_compact_L64_p9728.md
-    "ising_L64_compact": {"source": "7239a44f398aea87", "inst_per_attempt": 1.956,
-                          "shared_wavefronts_per_attempt": 0.381, "traffic_bytes_per_launch": 5170},
+    "ising_L64_compact": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 1.904,
+                          "shared_wavefronts_per_attempt": 0.365, "traffic_bytes_per_launch": 5173504},
     # Ising 64x64, compact staging with the 16-bit table, three blocks per SM
     # (p = 14592): profiles/ising_ws_t16_L64_p14592.md
-    "ising_L64_t16": {"source": "610fd672c5d9f3bc", "inst_per_attempt": 1.971,
-                      "shared_wavefronts_per_attempt": 0.372, "traffic_bytes_per_launch": 7665408},
-    # 8-Potts 32x32 (p = 4096): profiles/potts_ws_sweep_L32_p4096.md
-    "potts_L32": {"source": "7239a44f398aea87", "inst_per_attempt": 3.441, "shared_wavefronts_per_attempt": 0.521,
-                  "traffic_bytes_per_launch": 4321792},
+    "ising_L64_t16": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 1.989,
+                      "shared_wavefronts_per_attempt": 0.356, "traffic_bytes_per_launch": 7665664},
+    # 8-Potts 32x32 (p = 4096: 152 blocks of 27 chains): profiles/potts_ws_sweep_L32_p4096.md
+    "potts_L32": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 3.179, "shared_wavefronts_per_attempt": 0.582,
+                  "traffic_bytes_per_launch": 5121792},
 }
 # cycles per site of the Ising stream decider's loop run alone on one warp
 # (tests/gpu_decider_loop.cu, profiles/ising_decider_loop_replica.md)
@@ -81,6 +83,13 @@ def sweep_source_sha16():
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def sweep_blocks(p, n_sm):
+    """Blocks of a warp-specialised sweep launch: groups of 32 chains, or, while that
+    leaves SMs idle, the chains spread over every SM (ceil(p / SMs) chains per block)."""
+    cpg = 32 if (p + 31) // 32 >= n_sm else (p + n_sm - 1) // n_sm
+    return (p + cpg - 1) // cpg
 
 
 def counters(name):
@@ -358,8 +367,7 @@ def sweep_roofline(w, sweep_avg_ms, n_sm, sm_max):
     inst = c["inst_per_attempt"]
     achieved = inst * rate                                   # Gwarp-inst/s
     ok = c["matches_source"]
-    blocks = (w["p"] + 31) // 32
-    occupied = min(4 * n_sm, 4 * blocks)
+    occupied = min(4 * n_sm, 4 * sweep_blocks(w["p"], n_sm))
     latency = w["p"] * sm_max * 1e6 / DECIDER_CYCLES_PER_ATTEMPT_ALONE / 1e9
     return {
         "bound": "alu", "achieved": achieved if ok else None, "peak": peak, "unit": "Gwarp-inst/s",
@@ -492,7 +500,7 @@ def other_workloads(m, torch, stream, n_sm, sm_max):
                                    "frac": rnd(rate * c["inst_per_attempt"] / peak, 3) if c["matches_source"]
                                    else None,
                                    "counters_match_source": c["matches_source"],
-                                   "occupied_sms": min(n_sm, w["p"] // 32)}
+                                   "occupied_sms": min(n_sm, sweep_blocks(w["p"], n_sm))}
             beta0 = workloads.ISING_BETA0 if w["model"] == workloads.ISING else workloads.POTTS8_BETA0
             lnw = workloads.canonical_lnw(w["model"], w["L"], w.get("fixed_beta", beta0))
             g.set_lnw(lnw - lnw.max())
