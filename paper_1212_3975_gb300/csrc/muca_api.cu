@@ -261,10 +261,17 @@ int muca_init(muca_ctx **out, int model, int L, int q, int p, uint64_t seed, con
     // energy ensemble, automatic block size) spread the chains over every SM, cpg per
     // block.  A chain's attempts are sequential, so at small p the chains' own latency
     // bounds the rate, and fewer chains per SM contend less for its shared memory.
+    // Only where the plan stages the lattices in shared memory: a block's chains then
+    // span part of a cache line of the chain-interleaved lattice, which in global
+    // memory costs more lines per warp access than it gains (8-Potts 128x128 at
+    // p = 4096: 35 attempts/ns spread against 70 with 32 chains per block).
     c->cpg = 32;
-    if (L % 4 == 0 && c0.ensemble == MUCA_ENSEMBLE_ENERGY && c0.chains_per_block == 0 && (p + 31) / 32 < c->n_sm)
+    c->p_pad = (p + 31) / 32 * 32;
+    if (L % 4 == 0 && c0.ensemble == MUCA_ENSEMBLE_ENERGY && c0.chains_per_block == 0 && (p + 31) / 32 < c->n_sm &&
+        plan_sweeps(c).lattice_smem) {
         c->cpg = (p + c->n_sm - 1) / c->n_sm;
-    c->p_pad = (p + c->cpg - 1) / c->cpg * 32;
+        c->p_pad = (p + c->cpg - 1) / c->cpg * 32;
+    }
     int rc = alloc_buffers(c);
     if (rc) {
         free_ctx(c);
