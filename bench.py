@@ -56,7 +56,8 @@ COUNTERS = {
     # warp issue too, so these counts are per attempt of a real chain):
     # profiles/ising_ws_sweep_L64_p1024.md
     "ising_L64": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 8.508,
-                  "shared_wavefronts_per_attempt": 1.013, "traffic_bytes_per_launch": 2564864},
+                  "shared_wavefronts_per_attempt": 1.013, "traffic_bytes_per_launch": 2564864,
+                  "chains_per_block": 7},
     # Ising 64x64, compact staging, two blocks per SM (p = 9728):
     # profiles/ising_ws_compact_L64_p9728.md
     "ising_L64_compact": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 1.904,
@@ -85,10 +86,14 @@ def sweep_source_sha16():
     return h.hexdigest()[:16]
 
 
+def chains_per_block(p, n_sm):
+    """Chains per block of a warp-specialised sweep launch with the lattices staged in
+    shared memory: 32, or, while groups of 32 leave SMs idle, ceil(p / SMs)."""
+    return 32 if (p + 31) // 32 >= n_sm else (p + n_sm - 1) // n_sm
+
+
 def sweep_blocks(p, n_sm):
-    """Blocks of a warp-specialised sweep launch: groups of 32 chains, or, while that
-    leaves SMs idle, the chains spread over every SM (ceil(p / SMs) chains per block)."""
-    cpg = 32 if (p + 31) // 32 >= n_sm else (p + n_sm - 1) // n_sm
+    cpg = chains_per_block(p, n_sm)
     return (p + cpg - 1) // cpg
 
 
@@ -415,6 +420,12 @@ def p_sweep(m, torch, stream, n_sm, sm_max):
         c = counters("ising_L64_t16" if plan & m.MUCA_PLAN_TABLE16 else
                      "ising_L64_compact" if plan & m.MUCA_PLAN_COMPACT else "ising_L64")
         ok = c["matches_source"]
+        if "chains_per_block" in c:
+            # a warp issues for all 32 lanes: per attempt of a chain the counts scale
+            # with 1 / (chains per block) from the captured launch's
+            scale = c["chains_per_block"] / chains_per_block(p, n_sm)
+            c["inst_per_attempt"] *= scale
+            c["shared_wavefronts_per_attempt"] *= scale
         out.append({"p": p, "attempts_per_ns": rnd(rate), "compact": bool(plan & m.MUCA_PLAN_COMPACT),
                     "blocks_per_sm": 3 if plan & m.MUCA_PLAN_TABLE16 else 2 if plan & m.MUCA_PLAN_COMPACT else 1,
                     "issue_frac": rnd(rate * c["inst_per_attempt"] / peak, 3) if ok else None,
