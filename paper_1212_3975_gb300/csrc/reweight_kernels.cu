@@ -612,13 +612,16 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int total = r.off[n_tiles];
     const int dstep = model == MUCA_ISING ? 4 : 1;  // energy step between neighbouring bins
+    const int n_bins = model == MUCA_ISING ? V + 1 : 2 * V + 1;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int T = r.item_tile[item];
         const TileParams tp = r.tiles[T];
         const int chunk = item - r.off[T];
         const int j0 = T * kRwTile, nt = min(kRwTile, n_beta - j0);
         const int b0 = tp.lo + chunk * tp.ch;
-        const int b1 = min(b0 + tp.ch, tp.lo + tp.nch * tp.ch);
+        // chunks are whole multiples of 32 bins: the last one may reach past the last
+        // bin, where the per-bin arrays end (the next array follows directly)
+        const int b1 = min(min(b0 + tp.ch, tp.lo + tp.nch * tp.ch), n_bins);
         if (FP64) {
             double cd[kRwTile], dbd[kRwTile];
 #pragma unroll

@@ -52,6 +52,28 @@ def test_reweight_full_grid(muca, name):
         assert v <= BOUNDS[prec], (name, prec, k, v)
 
 
+@pytest.mark.parametrize("model,L", [(workloads.ISING, 4), (workloads.ISING, 8), (workloads.ISING, 12),
+                                     (workloads.POTTS, 4), (workloads.POTTS, 6)])
+def test_reweight_windows_at_the_top_bin(muca, model, L):
+    """Flat sums over every bin up to the top of the energy range on small lattices: a
+    tile's window then ends at the last bin, and its chunks (whole multiples of 32 bins)
+    reach past it.  Every precision against the oracle, all values finite."""
+    q = 2 if model == workloads.ISING else 8
+    n, s1, s2, lnw = workloads.synthetic_samples(model, L, "flat", 200000, 31)
+    assert n[-1] > 0                       # the top bin is sampled
+    betas = np.linspace(0.3, 0.6, 40) if model == workloads.ISING else np.linspace(1.2, 1.4, 40)
+    ref = reweight.reweight_binned(model, L, q, lnw, n, s1, s2, betas)
+    with muca.Muca(model, L, q, 8, 1) as g:
+        g.set_lnw(lnw)
+        g.set_samples(n, s1, s2)
+        for prec in ("fp64", "fp32", "bf16"):
+            r = g.reweight(betas, prec)
+            for k in ("e", "C", "absm", "chi"):
+                assert np.all(np.isfinite(r[k])), (prec, k)
+                rel = np.abs(r[k] - ref[k]) / np.maximum(np.abs(ref[k]), 1e-300)
+                assert rel.max() <= BOUNDS[prec], (prec, k, float(rel.max()))
+
+
 def test_set_samples_equals_production(muca):
     """Production sums injected through muca_set_samples reweight exactly as the same
     sums accumulated by muca_produce."""
