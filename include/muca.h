@@ -209,12 +209,12 @@ int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
  *   lnw [n_bins] FP64 (the weights the samples were produced with), betas [n_beta],
  *   out [4][n_beta] FP64 (rows e, C, absm, chi); precision MUCA_FP64 or MUCA_FP32;
  *   work is queued on cuda_stream (NULL = legacy default stream).
- * Its scratch is one fixed array inside the library's device image, 1,798,144 bytes:
+ * Its scratch is one fixed array inside the library's device image, 1,806,336 bytes:
  * per-bin arrays for up to 16385 bins and the tile sums of 512 betas (more betas are
  * taken 512 at a time); lattices with more than 16385 bins (Ising L > 128, 8-Potts
  * L > 90) are rejected with MUCA_ERR_ARG.  The image, and with it the array, is
  * loaded onto a GPU by the first call on that device (CUDA loads modules lazily by
- * default), so that first call needs 1,798,144 bytes of free device memory once and
+ * default), so that first call needs 1,806,336 bytes of free device memory once and
  * can fail with MUCA_ERR_CUDA when none is left: make it at start-up, before any
  * stream capture.  From then on the GPU holds the array until the process exits.
  * Every call looks the array's address up for the current device and context

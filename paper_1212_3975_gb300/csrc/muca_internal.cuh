@@ -240,12 +240,13 @@ constexpr size_t rw_bin_part_bytes(size_t nb)
     return rw_align256(5 * nb * 8) + 5 * rw_align256(nb * 4) + rw_align256(8 * ((nb + 255) / 256)) + 256;
 }
 // per-call part: tile parameters, shifts (FP64, and the float constants of every beta),
+// every beta's reference bin (mean |M| in FP64 and as a float pair),
 // item offsets, the tiles' completion counters (each zeroed by its setup block), the
 // tile of every item, partial sums
 constexpr size_t rw_tile_part_bytes(size_t n_beta)
 {
     return rw_align256(kRwTileParamsBytes * ((n_beta + kRwTile - 1) / kRwTile)) + rw_align256(8 * n_beta) +
-           rw_align256(16 * n_beta) +
+           rw_align256(16 * n_beta) + rw_align256(8 * n_beta) + rw_align256(8 * n_beta) +
            rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile + 1)) +
            rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile + 1)) +
            rw_align256(4 * ((n_beta + kRwTile - 1) / kRwTile) * kRwMaxChunks) +

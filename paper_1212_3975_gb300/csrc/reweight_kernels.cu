@@ -337,7 +337,10 @@ struct RwScratch {
     int nblk;
     TileParams *tiles;             // [n_tiles]
     double *c;                     // [n_beta] per-beta shift (ln units)
-    float4 *bc;                    // [n_beta] float constants: (beta - beta_T) log2 e as a pair, c log2 e
+    float4 *bc;                    // [n_beta] float constants: (beta - beta_T) log2 e as a pair, c log2 e,
+                                   //   and the beta's reference energy E_ref - E_T (an exact integer)
+    double *xref;                  // [n_beta] mean |M| of the beta's reference bin
+    float2 *xrf;                   //   and as a float pair
     int *off;                      // [n_tiles + 1] item offsets of the tiles
     unsigned *cnt0;                // completion counter of the setup kernel (zero between calls)
     unsigned *cnt;                 // [n_tiles] completion counters of the tiles (zeroed by the setup)
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
                                                        Observables o)
 {
     __shared__ float s_v[8], s_m[8][kRwTile];
-    __shared__ int s_i[8], s_lo[8], s_hi[8];
+    __shared__ int s_i[8], s_lo[8], s_hi[8], s_mi[8][kRwTile];
     __shared__ int s_last;
     const int T = blockIdx.x, j0 = T * kRwTile, nt = min(kRwTile, n_beta - j0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -510,12 +513,18 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
         dbmax = fmaxf(dbmax, fabsf(db[t]));
     }
     // pass 2: the window (bins that can reach e^-100 of the largest weight for some beta
-    // of the tile, approximate exponents with 2 units of margin) and every beta's
-    // maximum exponent (attained inside the window)
+    // of the tile, approximate exponents with 2 units of margin), and every beta's
+    // maximum exponent and the bin that attains it: the beta's own reference, around
+    // which its columns are centred (a tile may hold betas whose weights peak far apart;
+    // centred on one tile-wide bin, C and chi would cancel there)
     int lo = hi_s + 1, hi = lo_s - 1;
     float mx[kRwTile];
+    int mi[kRwTile];
 #pragma unroll
-    for (int t = 0; t < kRwTile; ++t) mx[t] = -INFINITY;
+    for (int t = 0; t < kRwTile; ++t) {
+        mx[t] = -INFINITY;
+        mi[t] = kT;
+    }
 #pragma unroll 2
     for (int b = lo_s + (int)threadIdx.x; b <= hi_s; b += 256) {
         const float l = r.lnOf[b];
@@ -524,20 +533,36 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
         const float G = (l - lTf) - bTf * dE;
         if (G + dbmax * fabsf(dE) >= (float)kCut - 2.f) { lo = min(lo, b); hi = max(hi, b); }
 #pragma unroll
-        for (int t = 0; t < kRwTile; ++t) mx[t] = fmaxf(mx[t], G - db[t] * dE);
+        for (int t = 0; t < kRwTile; ++t) {
+            const float v = G - db[t] * dE;
+            if (v > mx[t]) {
+                mx[t] = v;
+                mi[t] = b;
+            }
+        }
     }
     for (int k = 16; k > 0; k >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, k));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, k));
 #pragma unroll
-        for (int t = 0; t < kRwTile; ++t) mx[t] = fmaxf(mx[t], __shfl_xor_sync(0xffffffffu, mx[t], k));
+        for (int t = 0; t < kRwTile; ++t) {
+            const float ov = __shfl_xor_sync(0xffffffffu, mx[t], k);
+            const int oi = __shfl_xor_sync(0xffffffffu, mi[t], k);
+            if (ov > mx[t] || (ov == mx[t] && oi < mi[t])) {
+                mx[t] = ov;
+                mi[t] = oi;
+            }
+        }
     }
     __syncthreads();
     if (lane == 0) {
         s_lo[warp] = lo;
         s_hi[warp] = hi;
 #pragma unroll
-        for (int t = 0; t < kRwTile; ++t) s_m[warp][t] = mx[t];
+        for (int t = 0; t < kRwTile; ++t) {
+            s_m[warp][t] = mx[t];
+            s_mi[warp][t] = mi[t];
+        }
     }
     __syncthreads();
     lo = s_lo[0];
@@ -548,13 +573,24 @@ __global__ void __launch_bounds__(256) rw_setup_kernel(RwScratch r, const double
         hi = -1;
     }
     if ((int)threadIdx.x < nt) {
-        float m = s_m[0][threadIdx.x];
-        for (int w = 1; w < 8; ++w) m = fmaxf(m, s_m[w][threadIdx.x]);
-        const double c = -(double)m;         // per-beta shift (ln units)
-        r.c[j0 + threadIdx.x] = c;
-        const double db2 = (betas[j0 + threadIdx.x] - betaT) * kLog2e;
+        const int t = threadIdx.x, j = j0 + t;
+        float m = s_m[0][t];
+        int k = s_mi[0][t];
+        for (int w = 1; w < 8; ++w)
+            if (s_m[w][t] > m || (s_m[w][t] == m && s_mi[w][t] < k)) {
+                m = s_m[w][t];
+                k = s_mi[w][t];
+            }
+        const double c = -(double)m;  // per-beta shift (ln units)
+        r.c[j] = c;
+        const double db2 = (betas[j] - betaT) * kLog2e;
         const float dbh = (float)db2;
-        r.bc[j0 + threadIdx.x] = make_float4(dbh, (float)(db2 - (double)dbh), (float)(c * kLog2e), 0.f);
+        // the beta's reference: E_ref - E_T (an exact integer, also as a float) and the
+        // bin's mean |M|
+        const float dref = (float)(bin_energy(model, V, k) - ETd);
+        r.bc[j] = make_float4(dbh, (float)(db2 - (double)dbh), (float)(c * kLog2e), dref);
+        r.xref[j] = r.d.x1[k];
+        r.xrf[j] = make_float2(r.x1h[k], r.x1l[k]);
     }
     if (threadIdx.x == 0) {
         const int width = max(0, hi - lo + 1);
@@ -623,12 +659,14 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
         // bin, where the per-bin arrays end (the next array follows directly)
         const int b1 = min(min(b0 + tp.ch, tp.lo + tp.nch * tp.ch), n_bins);
         if (FP64) {
-            double cd[kRwTile], dbd[kRwTile];
+            double cd[kRwTile], dbd[kRwTile], drd[kRwTile], xrd[kRwTile];
 #pragma unroll
             for (int t = 0; t < kRwTile; ++t) {
                 const bool ok = t < nt;
                 cd[t] = ok ? r.c[j0 + t] : -1e300;
                 dbd[t] = ok ? betas[j0 + t] - tp.betaT : 0.0;
+                drd[t] = ok ? (double)r.bc[j0 + t].w : 0.0;
+                xrd[t] = ok ? r.xref[j0 + t] : 0.0;
             }
             double acc[kRwTile][6];
 #pragma unroll
@@ -640,13 +678,15 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
                 if (l == -INFINITY) continue;
                 const double dEd = (double)(dstep * (b - tp.kT));
                 const double G = __dsub_rn(__dsub_rn(l, tp.lnOT), __dmul_rn(tp.betaT, dEd));
-                const double dx = r.d.x1[b] - tp.x1T;
-                const double cols[6] = {1.0, dEd, dEd * dEd, dx, dx * dx, r.d.v[b]};
+                const double x1 = r.d.x1[b], vb = r.d.v[b];
 #pragma unroll
                 for (int t = 0; t < kRwTile; ++t) {
                     const double a = __fma_rn(-dbd[t], dEd, G + cd[t]);
                     if (a < kCut) continue;
                     const double w = exp(a);
+                    // columns centred on the beta's reference bin
+                    const double d = dEd - drd[t], dx = x1 - xrd[t];
+                    const double cols[6] = {1.0, d, d * d, dx, dx * dx, vb};
 #pragma unroll
                     for (int k = 0; k < 6; ++k) acc[t][k] = __fma_rn(w, cols[k], acc[t][k]);
                 }
@@ -668,13 +708,17 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
             }
         } else {
             // FP32 only: the tile's reference and every beta's constants come as floats
-            float dbh[kRwTile], dbl[kRwTile], chv[kRwTile];
+            float dbh[kRwTile], dbl[kRwTile], chv[kRwTile], drf[kRwTile], xrh[kRwTile], xrl[kRwTile];
 #pragma unroll
             for (int t = 0; t < kRwTile; ++t) {
                 const float4 kc = t < nt ? r.bc[j0 + t] : make_float4(0.f, 0.f, -1e30f, 0.f);
+                const float2 xr = t < nt ? r.xrf[j0 + t] : make_float2(0.f, 0.f);
                 dbh[t] = kc.x;
                 dbl[t] = kc.y;
                 chv[t] = kc.z;
+                drf[t] = kc.w;
+                xrh[t] = xr.x;
+                xrl[t] = xr.y;
             }
             const float L2h = (float)kLog2e, L2l = (float)(kLog2e - (double)(float)kLog2e);
             float hi[kRwTile][6], lo[kRwTile][6];
@@ -697,11 +741,7 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
                 const float glo = __fsub_rn(__fsub_rn(__fadd_rn(e2, dlo), pe), q);
                 const float Gh = __fmul_rn(g1, L2h);
                 const float Gl = __fadd_rn(__fmaf_rn(g1, L2h, -Gh), __fadd_rn(__fmul_rn(g1, L2l), __fmul_rn(glo, L2h)));
-                // mean |M| relative to the reference bin
-                float xa, xe;
-                two_sum(r.x1h[b], -tp.x1Th, xa, xe);
-                const float dxf = __fadd_rn(xa, __fadd_rn(xe, __fsub_rn(r.x1l[b], tp.x1Tl)));
-                const float cols[6] = {1.f, dE, __fmul_rn(dE, dE), dxf, __fmul_rn(dxf, dxf), r.vf[b]};
+                const float x1h = r.x1h[b], x1l = r.x1l[b], vb = r.vf[b];
 #pragma unroll
                 for (int t = 0; t < kRwTile; ++t) {
                     // a = (Gh + Gl) + c - (dbh + dbl) dE as a float pair
@@ -716,6 +756,13 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
                     const float al = __fsub_rn(rl, __fsub_rn(ah, s2));
                     const float w0 = exp2f(ah);
                     const float w = __fmaf_rn(w0, al * (float)kLn2, w0);
+                    // columns centred on the beta's reference bin: the energy offset is an
+                    // exact integer, the mean |M| a float pair
+                    const float d = __fsub_rn(dE, drf[t]);
+                    float xa, xe;
+                    two_sum(x1h, -xrh[t], xa, xe);
+                    const float dxf = __fadd_rn(xa, __fadd_rn(xe, __fsub_rn(x1l, xrl[t])));
+                    const float cols[6] = {1.f, d, __fmul_rn(d, d), dxf, __fmul_rn(dxf, dxf), vb};
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
                         float sum, err;
@@ -767,7 +814,8 @@ __global__ void __launch_bounds__(256) rw_sums_kernel(RwScratch r, const double 
                 for (int i = r.off[T]; i < r.off[T] + tp.nch; ++i)
 #pragma unroll
                     for (int k = 0; k < 6; ++k) S[k] += __ldcg(&r.part[((size_t)i * kRwTile + t) * 6 + k]);
-                write_obs(o, j0 + t, betas[j0 + t], tp.ET, tp.x1T, S[0], S[1], S[2], S[3], S[4], S[5], V, mnorm);
+                write_obs(o, j0 + t, betas[j0 + t], tp.ET + (double)r.bc[j0 + t].w, r.xref[j0 + t], S[0], S[1], S[2],
+                          S[3], S[4], S[5], V, mnorm);
             }
         }
     }
@@ -827,6 +875,10 @@ RwScratch carve(void *bins, size_t cap, size_t nb, void *tiles, int n_beta)
     pt += align256(sizeof(double) * n_beta);
     r.bc = reinterpret_cast<float4 *>(pt);
     pt += align256(sizeof(float4) * n_beta);
+    r.xref = reinterpret_cast<double *>(pt);
+    pt += align256(sizeof(double) * n_beta);
+    r.xrf = reinterpret_cast<float2 *>(pt);
+    pt += align256(sizeof(float2) * n_beta);
     r.off = reinterpret_cast<int *>(pt);
     pt += align256(sizeof(int) * (n_tiles + 1));
     r.cnt = reinterpret_cast<unsigned *>(pt);

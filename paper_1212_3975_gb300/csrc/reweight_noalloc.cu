@@ -10,7 +10,7 @@
 //
 // The array is part of this library's device image: once the image is loaded on a
 // GPU (with CUDA's default lazy loading, at the first call on that device, which
-// therefore needs kNoallocScratchBytes = 1,798,144 bytes of free device memory once;
+// therefore needs kNoallocScratchBytes = 1,806,336 bytes of free device memory once;
 // make that first call at start-up, before any stream capture), the GPU holds it until
 // the process exits.  Host code may not use the array's name as a device address;
 // every call looks the address up with cudaGetSymbolAddress for the current device, so
@@ -32,7 +32,7 @@ using muca::kNoallocMaxBins;
 // is written or cleared by the same call first, so nothing has to start at zero.
 static __device__ __align__(256) double g_noalloc_scratch[muca::kNoallocScratchBytes / sizeof(double)];
 static_assert(muca::kNoallocScratchBytes % sizeof(double) == 0, "scratch size");
-static_assert(muca::kNoallocScratchBytes == 1798144, "the documented size of the scratch");
+static_assert(muca::kNoallocScratchBytes == 1806336, "the documented size of the scratch");
 
 // device (or managed) memory that the current device `dev` can use
 bool device_pointer_on(const void *p, int dev)
