@@ -257,7 +257,11 @@ int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
  *                           in shared memory, three blocks per SM (Ising, L % 32 == 0,
  *                           L >= 64, more than two groups of 32 chains per SM); a
  *                           draw whose upper half ties the table entry replays its
- *                           word from the 32-bit table, so results are unchanged.
+ *                           word from the 32-bit table, so results are unchanged,
+ *  MUCA_PLAN_HIST16         block histogram of 16-bit counts in shared memory, two bins
+ *                           per word, added to the merged histogram every
+ *                           floor(65535 / (32 L)) rows (Ising histograms too large for
+ *                           32-bit counts in shared memory, e.g. 256 x 256).
  * Errors: MUCA_ERR_ARG (null context). */
 #define MUCA_PLAN_LATTICE_SMEM 1
 #define MUCA_PLAN_HIST_SMEM 2
@@ -266,6 +270,7 @@ int muca_get_iteration(const muca_ctx *ctx); /* weight iterations done */
 #define MUCA_PLAN_COMPACT 16
 #define MUCA_PLAN_WARP_SPECIALIZED 32
 #define MUCA_PLAN_TABLE16 64
+#define MUCA_PLAN_HIST16 128
 int muca_sweep_plan(const muca_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

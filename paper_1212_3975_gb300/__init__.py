@@ -11,7 +11,7 @@ import numpy as np
 
 from ._muca import (  # noqa: F401
     MUCA_BF16, MUCA_PLAN_COMPACT, MUCA_PLAN_HIST_SMEM, MUCA_PLAN_LATTICE_SMEM, MUCA_PLAN_PAIR_HIST,
-    MUCA_PLAN_TABLE16, MUCA_PLAN_TABLE_SMEM, MUCA_PLAN_WARP_SPECIALIZED,
+    MUCA_PLAN_HIST16, MUCA_PLAN_TABLE16, MUCA_PLAN_TABLE_SMEM, MUCA_PLAN_WARP_SPECIALIZED,
     MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION, MUCA_FP32, MUCA_FP64, MUCA_ISING, MUCA_POTTS, MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE, MUCA_STAGING_AUTO, MUCA_STAGING_GLOBAL,
     MUCA_STAGING_SHARED,
     MucaConfig, MucaError, MucaIterStats, MucaJob, check, declared_symbols, lib)

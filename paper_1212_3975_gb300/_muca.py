@@ -19,7 +19,7 @@ MUCA_RECURSION_ACCUMULATED, MUCA_RECURSION_SIMPLE = 0, 1
 MUCA_STAGING_AUTO, MUCA_STAGING_SHARED, MUCA_STAGING_GLOBAL = 0, 1, 2
 MUCA_ENSEMBLE_ENERGY, MUCA_ENSEMBLE_MAGNETIZATION = 0, 1
 MUCA_PLAN_LATTICE_SMEM, MUCA_PLAN_HIST_SMEM, MUCA_PLAN_TABLE_SMEM, MUCA_PLAN_PAIR_HIST = 1, 2, 4, 8
-MUCA_PLAN_COMPACT, MUCA_PLAN_WARP_SPECIALIZED, MUCA_PLAN_TABLE16 = 16, 32, 64
+MUCA_PLAN_COMPACT, MUCA_PLAN_WARP_SPECIALIZED, MUCA_PLAN_TABLE16, MUCA_PLAN_HIST16 = 16, 32, 64, 128
 
 ERROR_NAMES = {-1: "MUCA_ERR_ARG", -2: "MUCA_ERR_CUDA", -3: "MUCA_ERR_OOM",
                -4: "MUCA_ERR_TIMEOUT", -5: "MUCA_ERR_STATE", -6: "MUCA_ERR_IO"}

@@ -106,6 +106,7 @@ struct SweepPlan {
     bool warp_specialized;  // decider / producer / bookkeeper warps per 32 chains
     bool compact;           // warp-specialised Ising: two blocks per SM (3-slot draw ring)
     bool t16;               // compact with a table of 16-bit threshold halves: three blocks per SM
+    bool hist16;            // histogram of 16-bit counts, two bins per word, flushed by rows
     int chains_per_block;
     size_t smem_bytes;      // staging of the plan (table, histogram, lattices)
     size_t table_bytes, hist_bytes, lat_bytes;  // its parts (0: not staged)

@@ -442,6 +442,7 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
     SweepPlan pl;
     pl.compact = false;
     pl.t16 = false;
+    pl.hist16 = false;
     int cpb = ctx->cfg.chains_per_block;
     if (cpb <= 0) {
         // Spread the chains over the SMs: one warp per block while that leaves SMs
@@ -466,19 +467,30 @@ SweepPlan plan_sweeps(const muca_ctx *ctx, bool allow_pairs, bool allow_compact)
     pl.table_smem = table <= 96 * 1024;
     if (pl.table_smem) used += table;
     pl.hist_smem = used + hist <= 160 * 1024;
-    if (pl.hist_smem) used += hist;
+    // Ising histograms too large for 32-bit counts in shared memory (256 x 256: 262 KB):
+    // 16-bit counts, two bins per word, flushed into the merged histogram by rows
+    // (otherwise every bin change of a chain is a global atomic) -- where the lattices
+    // cannot be staged in shared memory anyway, so that the histogram takes no room from
+    // them (at 224 x 224 they fit, and staging them is worth more to thermalisation and
+    // production than the 16-bit counts to the iterations)
     const int staging = ctx->cfg.staging;
+    const size_t hist16 = ((((size_t)ctx->n_bins + 1) / 2 * 4 + 15) & ~(size_t)15) + 128;
+    if (!pl.hist_smem && ws && ctx->model == MUCA_ISING && staging != MUCA_STAGING_SHARED && used + lat > cap &&
+        used + hist16 <= 160 * 1024)
+        pl.hist_smem = pl.hist16 = true;  // (the table is in global memory here too)
+    if (pl.hist_smem) used += pl.hist16 ? hist16 : hist;
     pl.lattice_smem = staging == MUCA_STAGING_SHARED || (staging == MUCA_STAGING_AUTO && used + lat <= cap);
     if (pl.lattice_smem) used += lat;
     // warp-specialised launches: the histogram of attempt pairs (one count per bin
     // change of a single attempt: 5 for Ising, 9 for Potts) when it fits beside the
     // table and the lattices
     const size_t pairs = (((size_t)ctx->n_bins * width * 4 + 15) & ~(size_t)15) + 128;
-    pl.hist_pairs = allow_pairs && ws && pl.table_smem && pl.hist_smem && pl.lattice_smem && used - hist + pairs <= cap;
+    pl.hist_pairs = allow_pairs && ws && !pl.hist16 && pl.table_smem && pl.hist_smem && pl.lattice_smem &&
+                    used - hist + pairs <= cap;
     if (pl.hist_pairs) used += pairs - hist;
     pl.smem_bytes = used;
     pl.table_bytes = pl.table_smem ? table : 0;
-    pl.hist_bytes = pl.hist_smem ? (pl.hist_pairs ? pairs : hist) : 0;
+    pl.hist_bytes = pl.hist_smem ? (pl.hist_pairs ? pairs : pl.hist16 ? hist16 : hist) : 0;
     pl.lat_bytes = pl.lattice_smem ? lat : 0;
     // More groups of 32 chains than SMs (the throughput regime): a plan whose block
     // takes more than half of an SM's shared memory runs one block per SM and leaves
@@ -530,7 +542,7 @@ int plan_flags(const SweepPlan &pl)
     return (pl.lattice_smem ? MUCA_PLAN_LATTICE_SMEM : 0) | (pl.hist_smem ? MUCA_PLAN_HIST_SMEM : 0) |
            (pl.table_smem ? MUCA_PLAN_TABLE_SMEM : 0) | (pl.hist_pairs ? MUCA_PLAN_PAIR_HIST : 0) |
            (pl.compact ? MUCA_PLAN_COMPACT : 0) | (pl.warp_specialized ? MUCA_PLAN_WARP_SPECIALIZED : 0) |
-           (pl.t16 ? MUCA_PLAN_TABLE16 : 0);
+           (pl.t16 ? MUCA_PLAN_TABLE16 : 0) | (pl.hist16 ? MUCA_PLAN_HIST16 : 0);
 }
 
 int launch_sweeps(muca_ctx *ctx, uint32_t phase, int n_sweeps, uint32_t sweep0, uint32_t iteration, bool hist,

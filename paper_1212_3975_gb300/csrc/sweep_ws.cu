@@ -54,6 +54,12 @@ cudaError_t ws_staging(const SweepArgs &a, const SweepPlan &pl, int blocks, size
         return launch_ws<MODEL, HIST, RECORD, true, HIST ? 1 : 0, false, kCompactRing, true>(a, blocks, smem, st);
     if (MODEL == MUCA_ISING && pl.compact)
         return launch_ws<MODEL, HIST, RECORD, true, HIST ? 1 : 0, false, kCompactRing>(a, blocks, smem, st);
+    // 16-bit counts (Ising histograms too large for 32-bit counts; the table and the
+    // lattices are then in global memory too)
+    if (MODEL == MUCA_ISING && pl.hist16) {
+        if (pl.table_smem || pl.lattice_smem) return cudaErrorInvalidConfiguration;  // not planned
+        return launch_ws<MODEL, HIST, RECORD, false, HIST ? 3 : 0, false>(a, blocks, smem, st);
+    }
     const int key = (pl.table_smem ? 4 : 0) | ((HIST && pl.hist_smem) ? 2 : 0) | (pl.lattice_smem ? 1 : 0);
     switch (key) {
     case 0: return launch_ws<MODEL, HIST, RECORD, false, 0, false>(a, blocks, smem, st);

@@ -383,7 +383,10 @@ __device__ __forceinline__ void ising_decide_stream(const SweepArgs &a, uint32_t
 // (2): C[b][d + 2] counts the pairs whose first attempt ends in bin b and whose second
 // ends in bin b + d (|d| <= 2), and the histogram is H[b] = sum_d C[b][d + 2] +
 // sum_d C[b - d][d + 2].  Mode 2 halves the shared-memory atomics, which otherwise
-// delay the decider's table loads.
+// delay the decider's table loads.  Mode 3 (lattices whose 32-bit histogram does not
+// fit in shared memory, e.g. 256 x 256): 16-bit counts, two bins per word, added to the
+// global histogram and cleared by the bookkeeper every floor(65535 / (32 L)) rows, before
+// any count can reach 2^16 (a row adds at most 32 L counts to one bin).
 // RU: slots of the draw ring (4; 3 in the compact staging that fits two blocks per SM)
 // T16: the shared table holds the upper 16 bits of the thresholds (compact staging of
 // three blocks per SM; rows of whole words, at least two per row: the stream decider)
@@ -402,7 +405,8 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
     const int n_tab = a.n_bins * 5;
     constexpr uint32_t ROWB = T16 ? 10u : 20u;  // table bytes per bin
     uint32_t *s_tab = smem;
-    const int n_hist = HPAIR ? a.n_bins * 5 : a.n_bins;
+    constexpr bool H16 = HIST && HMODE == 3;
+    const int n_hist = HPAIR ? a.n_bins * 5 : H16 ? (a.n_bins + 1) >> 1 : a.n_bins;
     const int tab_words = T16 ? (n_tab + 1) >> 1 : n_tab;
     uint32_t *s_hist = smem + (TSMEM ? ((tab_words + 3) & ~3) : 0);
     // the histogram is followed by one slot per lane (kHistDummy) for inactive lanes
@@ -724,6 +728,22 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
         int run_bin = bin;
         uint32_t run = 0;
         int it = 0;
+        // mode 3: rows between flushes of the 16-bit counts into the global histogram
+        const int flush_rows = max(1, 65535 / (32 * L));
+        int rows = 0;
+        auto flush16 = [&]() {
+            __syncwarp();  // every lane's counts of the flushed rows are in place
+            for (int i = lane; i < n_hist; i += 32) {
+                const uint32_t v = s_hist[i];
+                if (v) {
+                    s_hist[i] = 0u;
+                    unsigned long long *Hg = reinterpret_cast<unsigned long long *>(a.H) + 2 * i;
+                    if (v & 0xFFFFu) atomicAdd(Hg, (unsigned long long)(v & 0xFFFFu));
+                    if (v >> 16) atomicAdd(Hg + 1, (unsigned long long)(v >> 16));
+                }
+            }
+            __syncwarp();
+        };
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             for (int y = 0; y < L; ++y) {
                 uint32_t pflip = 0u;  // flip of the previous site in this row
@@ -741,7 +761,9 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                         const int nneq = (int)(((sn.lo >> j) & 1u) + 2u * ((sn.hi >> j) & 1u) + ((qn >> j) & 1u));
                         const bool acc = (sn.flip >> j) & 1u;
                         bin += acc ? 2 - nneq : 0;
-                        if (HIST && HSMEM) {
+                        if (H16) {
+                            red_shared(active ? s_hist + (bin >> 1) : s_hdummy, 1u << ((bin & 1) << 4));
+                        } else if (HIST && HSMEM) {
                             red_shared(active ? s_hist + bin : s_hdummy, 1u);
                         } else if (HIST && active) {
                             if (bin != run_bin) {
@@ -783,6 +805,10 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                     }
                     pflip = (sn.flip >> (nb - 1)) & 1u;
                 }
+                if (H16 && ++rows == flush_rows) {
+                    flush16();
+                    rows = 0;
+                }
             }
             if (RECORD && active) {
                 const int E = 4 * bin - 2 * V;
@@ -821,6 +847,14 @@ __device__ __forceinline__ void ising_ws_body(const SweepArgs &a, const int cblk
                 if (b - d >= 0 && b - d < a.n_bins) v += s_hist[5 * (b - d) + 2 + d];
             }
             if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&a.H[b]), (unsigned long long)v);
+        }
+    } else if (H16) {
+        // the counts since the last flush
+        for (int i = tid; i < n_hist; i += NT) {
+            const uint32_t v = s_hist[i];
+            unsigned long long *Hg = reinterpret_cast<unsigned long long *>(a.H) + 2 * i;
+            if (v & 0xFFFFu) atomicAdd(Hg, (unsigned long long)(v & 0xFFFFu));
+            if (v >> 16) atomicAdd(Hg + 1, (unsigned long long)(v >> 16));
         }
     } else if (HIST && HSMEM) {
         for (int i = tid; i < a.n_bins; i += NT) {

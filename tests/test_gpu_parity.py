@@ -206,6 +206,46 @@ def test_compact_staging_bit_exact(muca, L, per_sm):
     assert np.array_equal(n, on) and np.array_equal(s1, os1) and np.array_equal(s2, os2)
 
 
+@pytest.mark.parametrize("L,p", [(240, 9), (256, 40)])
+def test_hist16_bit_exact(muca, L, p):
+    """Ising histograms too large for 32-bit counts in shared memory, with lattices too
+    large to stage (L = 240: rows of partial words, the per-word decider; L = 256: the
+    stream decider): 16-bit counts, two bins per word, flushed into the merged histogram
+    every floor(65535 / (32 L)) rows (7 rows at L = 256: a 2-sweep iteration flushes 73
+    times).  Iteration histograms,
+    spins, E, M, thermalisation, production records and sums bit for bit against the
+    oracle."""
+    seed = 2718
+    lnw = random_weights(ISING, L, L + 9, 0.40)
+    thr = weights.thresholds(ISING, L, lnw)
+    with muca.Muca(ISING, L, 2, p, seed) as g:
+        plan = g.plan()
+        assert plan & muca.MUCA_PLAN_HIST16 and plan & muca.MUCA_PLAN_HIST_SMEM, plan
+        assert not plan & muca.MUCA_PLAN_TABLE_SMEM and not plan & muca.MUCA_PLAN_LATTICE_SMEM, plan
+        g.set_thresholds(thr)
+        H1 = g.iterate(2)
+        H2 = g.iterate(1)
+        spins = g.get_spins()
+        E, M = g.get_energies()
+        g.set_lnw(lnw)
+        g.set_thresholds(thr)
+        g.thermalize(1)
+        Er, Mr = g.produce(2)
+        n, s1, s2 = g.get_samples()
+    o = MucaOracle(ISING, L, 2, p, seed)
+    h1 = o.iterate(2, thr=thr)
+    h2 = o.iterate(1, thr=thr)
+    assert int(H1.sum()) == 2 * p * L * L
+    assert np.array_equal(H1, h1) and np.array_equal(H2, h2)
+    assert np.array_equal(spins, o.spins)
+    assert np.array_equal(E, o.E) and np.array_equal(M, o.M)
+    o.thermalize(1, thr=thr)
+    er, mr = o.produce(2, thr=thr)
+    assert np.array_equal(Er, er) and np.array_equal(Mr, mr)
+    on, os1, os2 = reweight.bin_series(ISING, L, er, mr)
+    assert np.array_equal(n, on) and np.array_equal(s1, os1) and np.array_equal(s2, os2)
+
+
 @pytest.mark.parametrize("model,L,p,accumulated", [(ISING, 8, 16, True), (ISING, 8, 16, False),
                                                    (POTTS, 6, 24, True), (ISING, 32, 40, True)])
 def test_update_matches_oracle_given_histogram(muca, model, L, p, accumulated):
