@@ -55,20 +55,20 @@ COUNTERS = {
     # Ising 64x64, p = 1024: 147 blocks of 7 chains, one per SM (the idle lanes of each
     # warp issue too, so these counts are per attempt of a real chain):
     # profiles/ising_ws_sweep_L64_p1024.md
-    "ising_L64": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 8.508,
-                  "shared_wavefronts_per_attempt": 1.013, "traffic_bytes_per_launch": 2564864,
+    "ising_L64": {"source": "8726118ec7318e9e", "inst_per_attempt": 8.508,
+                  "shared_wavefronts_per_attempt": 1.013, "traffic_bytes_per_launch": 2565120,
                   "chains_per_block": 7},
     # Ising 64x64, compact staging, two blocks per SM (p = 9728):
     # profiles/ising_ws_compact_L64_p9728.md
-    "ising_L64_compact": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 1.904,
-                          "shared_wavefronts_per_attempt": 0.365, "traffic_bytes_per_launch": 5173504},
+    "ising_L64_compact": {"source": "8726118ec7318e9e", "inst_per_attempt": 1.904,
+                          "shared_wavefronts_per_attempt": 0.365, "traffic_bytes_per_launch": 5169920},
     # Ising 64x64, compact staging with the 16-bit table, three blocks per SM
     # (p = 14592): profiles/ising_ws_t16_L64_p14592.md
-    "ising_L64_t16": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 1.989,
+    "ising_L64_t16": {"source": "8726118ec7318e9e", "inst_per_attempt": 1.989,
                       "shared_wavefronts_per_attempt": 0.356, "traffic_bytes_per_launch": 7665664},
     # 8-Potts 32x32 (p = 4096: 152 blocks of 27 chains): profiles/potts_ws_sweep_L32_p4096.md
-    "potts_L32": {"source": "ec2ba0f00ce6bd75", "inst_per_attempt": 3.179, "shared_wavefronts_per_attempt": 0.582,
-                  "traffic_bytes_per_launch": 5121792},
+    "potts_L32": {"source": "8726118ec7318e9e", "inst_per_attempt": 3.179, "shared_wavefronts_per_attempt": 0.582,
+                  "traffic_bytes_per_launch": 5122304},
 }
 # cycles per site of the Ising stream decider's loop run alone on one warp
 # (tests/gpu_decider_loop.cu, profiles/ising_decider_loop_replica.md)
@@ -684,9 +684,10 @@ def make_summary(r):
 
 
 def run_probe(args):
-    """One small launch of a workload's weight-iteration sweeps, for profiler captures:
-    start, a 2-sweep iteration and update (the launch skipped by -s 1), then one
-    iteration of --probe-sweeps sweeps (the captured launch)."""
+    """One small launch of a workload's sweeps, for profiler captures: start, a 2-sweep
+    iteration and update (the launch skipped by -s 1), then one iteration of
+    --probe-sweeps sweeps (the captured launch); with --probe-phase produce, a 2-sweep
+    thermalisation (skipped) and production sweeps at the workload's weights."""
     import torch
     import paper_1212_3975_gb300 as m
     from paper_1212_3975_gb300 import build as b
@@ -698,14 +699,21 @@ def run_probe(args):
     if w.get("fixed_beta"):
         lnw = workloads.canonical_lnw(w["model"], w["L"], w["fixed_beta"])
         g.set_lnw(lnw - lnw.max())
-    g.iterate(2)
-    g.update_weights()
+    if args.probe_phase == "produce":
+        g.thermalize(2)          # at the workload's weights
+    else:
+        g.iterate(2)
+        g.update_weights()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.iterate(args.probe_sweeps)
+    if args.probe_phase == "produce":
+        g.produce(args.probe_sweeps, None, None)
+    else:
+        g.iterate(args.probe_sweeps)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    print(json.dumps({"probe": args.probe, "p": w["p"], "plan": g.plan(), "sweeps": args.probe_sweeps,
+    print(json.dumps({"probe": args.probe, "phase": args.probe_phase, "p": w["p"], "plan": g.plan(),
+                      "sweeps": args.probe_sweeps,
                       "attempts_per_ns": w["p"] * w["L"] * w["L"] * args.probe_sweeps / dt / 1e9}))
     g.close()
 
@@ -800,6 +808,8 @@ def main():
                     help="run one small sweep launch of a workload (for profiler captures)")
     ap.add_argument("--probe-sweeps", type=int, default=10)
     ap.add_argument("--probe-p", type=int, default=0, help="number of chains of the probe (default: the workload's)")
+    ap.add_argument("--probe-phase", default="iterate", choices=["iterate", "produce"],
+                    help="the captured launch: a weight iteration or production sweeps")
     args = ap.parse_args()
     if args.probe:
         run_probe(args)
