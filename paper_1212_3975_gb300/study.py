@@ -167,13 +167,17 @@ def fit_inverse_l(L_list, values):
 
 
 def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, production=4000,
-                  beta_range=(1.25, 1.45), seed0=3, m_factor=1.0):
+                  beta_range=(1.25, 1.45), seed0=3, m_factor=1.0, all_runs=False):
     """Order-disorder interface tension of the 8-state Potts model (Sec. 5) for every L:
     `runs` independent MUCA runs of p chains each, iterated to convergence together
     (muca_batch_converge at M = m_factor x Eq. 7's M_opt(L, p)); every converged run is thermalised,
     runs a production that keeps only the per-bin sums, and gives sigma_od(L) from the
     equal-height analysis of muca_interface_tension.  sigma_od(L) is the mean over the
-    converged runs; finally sigma_od(L) = sigma_inf + c/L is fitted.
+    converged runs; finally sigma_od(L) = sigma_inf + c/L is fitted.  With all_runs, the
+    runs that did not pass the flatness test within max_iterations also produce with
+    their last weights (the equal-height analysis needs weights that sample both phases,
+    not a flat histogram in one iteration); their values are reported apart
+    (sigma_od_all over every run whose production shows two peaks).
 
     Returns ({L: dict(M, converged, N_iter, beta_eqh, sigma_od, sigma_err)},
     (sigma_inf, c))."""
@@ -185,17 +189,19 @@ def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, pr
         b = MucaBatch(jobs)
         try:
             n_iter = b.converge(M, max_iterations)
-            sig, bet = [], []
+            sig, bet, sig_all = [], [], []
             for j in range(runs):
-                if n_iter[j] < 0:
+                if n_iter[j] < 0 and not all_runs:
                     continue
                 g = b.job(j)
                 g.thermalize(therm_sweeps)
                 check(lib().muca_produce(g.handle, production, None, None))
                 beta, ratio, peaks, sigma = g.interface_tension(*beta_range)
                 if math.isfinite(sigma):
-                    sig.append(sigma)
-                    bet.append(beta)
+                    sig_all.append(sigma)
+                    if n_iter[j] >= 0:
+                        sig.append(sigma)
+                        bet.append(beta)
         finally:
             b.close()
         conv = [int(x) for x in n_iter if x > 0]
@@ -204,6 +210,11 @@ def sigma_od_scan(L_list, p=16, runs=4, max_iterations=300, therm_sweeps=200, pr
                        "beta_eqh": float(np.mean(bet)) if bet else math.nan,
                        "sigma_od": float(np.mean(sig)) if sig else math.nan,
                        "sigma_err": float(np.std(sig, ddof=1) / math.sqrt(len(sig))) if len(sig) > 1 else math.nan}
+        if all_runs:
+            out[int(L)].update({"runs_with_two_peaks": len(sig_all),
+                                "sigma_od_all": float(np.mean(sig_all)) if sig_all else math.nan,
+                                "sigma_err_all": float(np.std(sig_all, ddof=1) / math.sqrt(len(sig_all)))
+                                if len(sig_all) > 1 else math.nan})
     # the 1/L fit needs at least three sizes
     Ls = [L for L in out if math.isfinite(out[L]["sigma_od"])]
     fit = fit_inverse_l(Ls, [out[L]["sigma_od"] for L in Ls]) if len(Ls) >= 3 else (math.nan, math.nan)
@@ -240,13 +251,19 @@ def main(argv=None):
     ap.add_argument("--factors", type=float, nargs="+", default=[0.5, 0.7, 1.0, 1.4, 2.0, 2.8, 4.0])
     ap.add_argument("--max-iterations", type=int, default=300)
     ap.add_argument("--production", type=int, default=4000)
+    ap.add_argument("--all-runs", action="store_true",
+                    help="sigma: also analyse the runs that did not converge (reported apart)")
     ap.add_argument("--model", choices=["ising", "potts"], default="ising")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     if a.what == "sigma":
         res, (s_inf, c) = sigma_od_scan(a.L, p=a.p[0], runs=a.runs, max_iterations=a.max_iterations,
-                                        production=a.production, m_factor=a.m_factor)
+                                        production=a.production, m_factor=a.m_factor, all_runs=a.all_runs)
         out = {"per_L": res, "sigma_inf": s_inf, "c": c}
+        if a.all_runs:
+            Ls = [L for L in res if math.isfinite(res[L]["sigma_od_all"])]
+            out["sigma_inf_all"], out["c_all"] = (fit_inverse_l(Ls, [res[L]["sigma_od_all"] for L in Ls])
+                                                  if len(Ls) >= 3 else (math.nan, math.nan))
     else:
         model = ISING if a.model == "ising" else POTTS
         per_L, (aa, bb) = eq7_scan(model, a.L, a.p, a.factors, a.seeds, a.max_iterations)
