@@ -190,9 +190,18 @@ int muca_set_samples(muca_ctx *ctx, const uint64_t *n, const uint64_t *sum_abs_m
  *   e    = <E>/V,  C = beta^2 (<E^2> - <E>^2)/V  (C_V of Sec. 5),
  *   absm = <|M|>/Mnorm,  chi = beta V (<m^2> - <|m|>^2),  m = M/Mnorm,
  * Mnorm = V (Ising) or (q-1) V (Potts); any output pointer may be NULL.
- * precision selects the arithmetic of the beta x E weight table and its contraction
- * (MUCA_FP64, MUCA_FP32, MUCA_BF16 on tensor cores); the per-beta log-sum-exp shift
- * and the final normalisations are FP64 in every mode.
+ * precision selects the arithmetic of the beta x E weight table and its contraction:
+ *  MUCA_FP64  exponents, weights and sums in FP64 (terms below e^-100 of a beta's
+ *             largest skipped);
+ *  MUCA_FP32  exponents and sums as float pairs (compensated), partial sums combined in
+ *             FP64: within ~2e-7 of FP64 on the configurations' beta grids;
+ *  MUCA_BF16  tensor cores: weights and columns split into three BF16 terms, FP32
+ *             accumulation flushed to FP64 per 16 bins.
+ * FP64 and FP32 centre every beta's columns on its own reference bin (the bin where its
+ * weights peak), so scattered or far betas are fine; BF16 centres each tile of 16
+ * consecutive betas on one bin (the columns are the shared operand of the product), so
+ * its C and chi are accurate only where a tile's betas peak close together, as on a
+ * dense sorted grid: use MUCA_FP32 otherwise.  Observables are formed in FP64.
  * Errors: MUCA_ERR_STATE (no records), MUCA_ERR_ARG. */
 int muca_reweight(muca_ctx *ctx, const double *betas, int n_beta, int precision,
                   double *e, double *C, double *absm, double *chi);
