@@ -15,10 +15,20 @@
 //   warps 1..3 (producers; 1..2 when warp 3 keeps the books): the Philox4x32-10
 //          draws (independent of the chain state) of each row word, written to a
 //          shared-memory ring ahead of the decider.
-//   warp 3 (bookkeeper, iteration and production launches): rebuilds from a
-//          per-word snapshot (neighbour sums, flip mask) every attempt's energy bin,
-//          fills the block histogram (one count per attempt, or per pair of
-//          consecutive attempts), and writes the (E, M) records.
+//   warp 3 (bookkeeper, iteration and production launches): rebuilds from
+//          snapshots (neighbour sums, flip mask; two row words per hand-off) every
+//          attempt's energy bin, fills the block histogram (one count per attempt, per
+//          pair of consecutive attempts, or 16-bit counts flushed by rows), and writes
+//          the (E, M) records.
+// A group holds up to 32 chains (fewer when small p is spread over every SM); the
+// stagings of the table, histogram and lattices range from everything in shared
+// memory (one block per SM) over the compact staging (two blocks per SM) to the
+// table of 16-bit threshold halves (three blocks per SM, ties replayed exactly).
+//
+// 8-state Potts (further below): decider, three producers (draws, proposals and the
+// byte-parallel column counts of the neighbours fixed in advance) and, for iterations
+// and production, a bookkeeper; rows of whole ring slots run the slot decider.
+//
 // Hand-offs use named barriers (bar.sync / bar.arrive) in the classic full/empty
 // pattern; every warp runs the same (sweep, row, word) loop nest, so the number of
 // arrivals and waits on each barrier match exactly.
