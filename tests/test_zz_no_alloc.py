@@ -71,6 +71,34 @@ def test_noalloc_matches_context_reweight(precision, tol):
         g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noalloc_several_passes(precision):
+    """More betas than one pass of the fixed scratch holds (512): 1100 betas in three
+    passes give exactly what muca_reweight gives in one call."""
+    torch = pytest.importorskip("torch")
+    import paper_1212_3975_gb300 as m
+    from paper_1212_3975_gb300 import build
+    build.build()
+    lib = m.lib()
+    g = _produce(m, m.MUCA_ISING, 16, 2, 0.42, seed=5)
+    betas = np.linspace(0.25, 0.6, 1100)
+    ref = g.reweight(betas, precision)
+    n, s1, s2 = g.get_samples()
+    samples = torch.tensor(np.stack([n, s1, s2]).view(np.int64), device="cuda")
+    lnw = torch.tensor(g.get_lnw(), device="cuda")
+    betas_d = torch.tensor(betas, device="cuda")
+    out = torch.full((4, len(betas)), float("nan"), dtype=torch.float64, device="cuda")
+    m.check(lib.muca_reweight_noalloc(m.MUCA_ISING, 16, 2, _ptr(samples), _ptr(lnw), _ptr(betas_d), len(betas),
+                                      m.PRECISIONS[precision], _ptr(out), None))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for row, key in enumerate(("e", "C", "absm", "chi")):
+        assert np.all(np.isfinite(got[row])), key
+        rel = np.abs(got[row] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
+        assert rel.max() <= 1e-12, (key, rel.max())
+    g.close()
+
+
 def test_noalloc_rejects_oversized_and_host_buffers():
     torch = pytest.importorskip("torch")
     import paper_1212_3975_gb300 as m
