@@ -73,6 +73,9 @@ COUNTERS = {
 # cycles per site of the Ising stream decider's loop run alone on one warp
 # (tests/gpu_decider_loop.cu, profiles/ising_decider_loop_replica.md)
 DECIDER_CYCLES_PER_ATTEMPT_ALONE = 36.6
+# the same for the 8-Potts slot decider (tests/gpu_potts_decider_loop.cu,
+# profiles/potts_decider_loop_replica.md)
+POTTS_DECIDER_CYCLES_PER_ATTEMPT_ALONE = 43.4
 # MUFU ex2 results per clock per SM (the special-function units: 4 per sub-partition
 # per clock); the FP32 reweighting evaluates one ex2 per contributing (beta, bin)
 MUFU_EX2_PER_CLK_PER_SM = 16
@@ -517,7 +520,12 @@ def other_workloads(m, torch, stream, n_sm, sm_max):
                                    "frac": rnd(rate * c["inst_per_attempt"] / peak, 3) if c["matches_source"]
                                    else None,
                                    "counters_match_source": c["matches_source"],
-                                   "occupied_sms": min(n_sm, sweep_blocks(w["p"], n_sm))}
+                                   "occupied_sms": min(n_sm, sweep_blocks(w["p"], n_sm)),
+                                   # p chains at the slot decider's cycles per attempt alone
+                                   "latency_bound_attempts_per_ns": rnd(
+                                       w["p"] * sm_max * 1e-3 / POTTS_DECIDER_CYCLES_PER_ATTEMPT_ALONE),
+                                   "frac_of_latency_bound": rnd(
+                                       rate / (w["p"] * sm_max * 1e-3 / POTTS_DECIDER_CYCLES_PER_ATTEMPT_ALONE), 3)}
             beta0 = workloads.ISING_BETA0 if w["model"] == workloads.ISING else workloads.POTTS8_BETA0
             lnw = workloads.canonical_lnw(w["model"], w["L"], w.get("fixed_beta", beta0))
             g.set_lnw(lnw - lnw.max())
