@@ -682,6 +682,7 @@ def make_summary(r):
     c3 = ow.get("potts8_L32_p4096", {})
     s["c3_iterate_attempts_per_ns"] = c3.get("iterate_attempts_per_ns")
     s["c3_issue_frac"] = c3.get("roofline", {}).get("frac")
+    s["c3_latency_frac"] = c3.get("roofline", {}).get("frac_of_latency_bound")
     s["c3_reweight_betas_per_s"] = {k: c3.get(k + "_betas_per_s") for k in ("fp64", "fp32", "bf16")}
     for name in ("ising_L256_p8192", "potts8_L128_p4096"):
         c5 = ow.get(name, {})
