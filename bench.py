@@ -55,20 +55,20 @@ COUNTERS = {
     # Ising 64x64, p = 1024: 147 blocks of 7 chains, one per SM (the idle lanes of each
     # warp issue too, so these counts are per attempt of a real chain):
     # profiles/ising_ws_sweep_L64_p1024.md
-    "ising_L64": {"source": "f9f6f6debffa1b88", "inst_per_attempt": 8.508,
+    "ising_L64": {"source": "8c638c33e6db10d8", "inst_per_attempt": 8.508,
                   "shared_wavefronts_per_attempt": 1.013, "traffic_bytes_per_launch": 2565120,
                   "chains_per_block": 7},
     # Ising 64x64, compact staging, two blocks per SM (p = 9728):
     # profiles/ising_ws_compact_L64_p9728.md
-    "ising_L64_compact": {"source": "f9f6f6debffa1b88", "inst_per_attempt": 1.904,
+    "ising_L64_compact": {"source": "8c638c33e6db10d8", "inst_per_attempt": 1.904,
                           "shared_wavefronts_per_attempt": 0.365, "traffic_bytes_per_launch": 5169920},
     # Ising 64x64, compact staging with the 16-bit table, three blocks per SM
     # (p = 14592): profiles/ising_ws_t16_L64_p14592.md
-    "ising_L64_t16": {"source": "f9f6f6debffa1b88", "inst_per_attempt": 1.989,
+    "ising_L64_t16": {"source": "8c638c33e6db10d8", "inst_per_attempt": 1.989,
                       "shared_wavefronts_per_attempt": 0.356, "traffic_bytes_per_launch": 7665664},
     # 8-Potts 32x32 (p = 4096: 152 blocks of 27 chains): profiles/potts_ws_sweep_L32_p4096.md
-    "potts_L32": {"source": "f9f6f6debffa1b88", "inst_per_attempt": 3.179, "shared_wavefronts_per_attempt": 0.582,
-                  "traffic_bytes_per_launch": 5122304},
+    "potts_L32": {"source": "8c638c33e6db10d8", "inst_per_attempt": 3.158, "shared_wavefronts_per_attempt": 0.582,
+                  "traffic_bytes_per_launch": 5122048},
 }
 # cycles per site of the Ising stream decider's loop run alone on one warp
 # (tests/gpu_decider_loop.cu, profiles/ising_decider_loop_replica.md)
